@@ -1,0 +1,84 @@
+"""Exact single-precision arithmetic on rationals, in pure Python.
+
+Used only by the tests, to brute-force tiny dwell maps without any C
+compiler, libm or hardware FMA in the loop: every operation is carried out
+exactly on ``fractions.Fraction`` values and then rounded once to the
+nearest float32 (ties to even), which is what IEEE 754 prescribes for a
+single-precision add, multiply and fused multiply-add.
+"""
+from fractions import Fraction
+import struct
+
+_HALF = Fraction(1, 2)
+
+
+def rn32(q):
+    """Round the rational ``q`` to the nearest float32 (ties to even)."""
+    q = Fraction(q)
+    if q == 0:
+        return Fraction(0)
+    sign = -1 if q < 0 else 1
+    a = -q if q < 0 else q
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    # normalise so that 2**e <= a < 2**(e+1)
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    quantum_exp = max(e - 23, -149)          # 24-bit significand; subnormals below 2**-126
+    scaled = a / Fraction(2) ** quantum_exp
+    fl = scaled.numerator // scaled.denominator
+    rem = scaled - fl
+    if rem > _HALF or (rem == _HALF and fl % 2 == 1):
+        fl += 1
+    res = fl * Fraction(2) ** quantum_exp
+    if res >= Fraction(2) ** 128:
+        raise OverflowError("float32 overflow in a brute-force case")
+    return sign * res
+
+
+def f32(x):
+    """The float32 value nearest to a Python number, as a Fraction."""
+    return rn32(Fraction(x))
+
+
+def to_float(q):
+    """A Fraction that is a float32 value, back to a Python float (exact)."""
+    v = float(q)
+    assert struct.unpack("f", struct.pack("f", v))[0] == v
+    return v
+
+
+def dwell(cr, ci, max_dwell, le=False):
+    """Dwell by exact rounding: the same definition as the C reference,
+    restated independently (continue while |z|^2 < 4, one update per pass)."""
+    cr, ci = f32(cr), f32(ci)
+    zr = zi = Fraction(0)
+    d = 0
+    while d < max_dwell:
+        zi2 = rn32(zi * zi)
+        m = rn32(zr * zr + zi2)
+        if not (m <= 4 if le else m < 4):
+            break
+        t = rn32(-zi * zi + cr)
+        nzr = rn32(zr * zr + t)
+        nzi = rn32(rn32(zr + zr) * zi + ci)
+        zr, zi = nzr, nzi
+        d += 1
+    return d
+
+
+def pixel_c(window, n, px, py):
+    re_min, re_max, im_min, im_max = (f32(v) for v in window)
+    dx = rn32(rn32(re_max - re_min) / n)
+    dy = rn32(rn32(im_max - im_min) / n)
+    return rn32(px * dx + re_min), rn32(py * dy + im_min)
+
+
+def exhaustive(window, n, max_dwell):
+    out = [[0] * n for _ in range(n)]
+    for py in range(n):
+        for px in range(n):
+            cr, ci = pixel_c(window, n, px, py)
+            out[py][px] = dwell(cr, ci, max_dwell)
+    return out

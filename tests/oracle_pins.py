@@ -1,0 +1,274 @@
+"""Pins of the CPU reference to facts fixed outside it.
+
+Each ``pin_*`` function takes an ``oracle.Oracle`` and raises
+``AssertionError`` when the reference disagrees with:
+
+* values hand-computed from the definition of the dwell (Sec. 6 of the paper:
+  z <- z^2 + c from z = 0, counted while |z| < 2), exact in float32;
+* an exact-rational brute force of tiny maps (``f32exact``), which shares no
+  code with the C reference and needs no libm or FMA hardware;
+* mathematics: conjugate symmetry of the set, its known area (about 1.5066),
+  the exact pixel -> c mapping where the spacing is a power of two;
+* structure that the subdivision rule of Sec. 4.2.1 fixes by hand on tiny
+  grids (region counts per level with fills disabled), and invariants of the
+  Mariani-Silver recursion on larger ones (tiling, uniform perimeters of
+  filled regions, stopping side B, leaf pixels equal the exhaustive map).
+
+``tests/test_oracle_pins.py`` runs them against the reference;
+``tests/test_oracle_mutants.py`` runs them against deliberately broken
+builds and expects each build to fail at least one.
+"""
+import os
+import random
+
+import numpy as np
+
+import f32exact
+
+C0_WINDOW = (-1.5, 0.5, -1.0, 1.0)
+ESCAPE_LE = 1
+NO_FILL = 2
+FILL, SUBDIVIDE, LEAF = 0, 1, 2
+
+
+# --------------------------------------------------------------------------
+# dwell of single points
+# --------------------------------------------------------------------------
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def closed_forms():
+    """Rows of ``golden/closed_forms.tsv``: (cr, ci, max_dwell, flags, dwell)."""
+    rows = []
+    with open(os.path.join(GOLDEN, "closed_forms.tsv")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            cr, ci, M, flags, d = line.split("\t")[:5]
+            rows.append((float(cr), float(ci), int(M), int(flags), int(d)))
+    return rows
+
+
+def pin_closed_forms(orc):
+    """Orbits followed by hand in exact float32 arithmetic, including the
+    strict (|z| < 2) and membership (|z| <= 2) readings of the escape test."""
+    rows = closed_forms()
+    assert len(rows) >= 20
+    for cr, ci, M, flags, d in rows:
+        assert orc.dwell(cr, ci, M, flags) == d, (cr, ci, M, flags, d)
+
+
+def pin_exact_points(orc):
+    """Random points against the exact-rational brute force."""
+    rng = random.Random(20220605)
+    for _ in range(150):
+        cr = f32exact.to_float(f32exact.f32(rng.uniform(-2.2, 1.0)))
+        ci = f32exact.to_float(f32exact.f32(rng.uniform(-1.4, 1.4)))
+        assert orc.dwell(cr, ci, 48) == f32exact.dwell(cr, ci, 48), (cr, ci)
+
+
+# --------------------------------------------------------------------------
+# maps
+# --------------------------------------------------------------------------
+def pin_exact_tiny_maps(orc):
+    """Tiny exhaustive maps, pixel for pixel, against the brute force; the
+    windows are asymmetric so a transposed map or swapped axis fails."""
+    cases = [((-2.0, 0.5, -1.1, 1.3), 1, 40), ((-2.0, 0.5, -1.1, 1.3), 2, 40),
+             ((-1.9, 0.6, -0.3, 1.2), 5, 30), ((-0.8, -0.6, 0.05, 0.30), 8, 60),
+             ((-2.0, 0.47, -1.12, 1.12), 7, 25)]
+    for win, n, M in cases:
+        got = orc.render_exhaustive(win, n, M, threads=2)
+        want = np.array(f32exact.exhaustive(win, n, M), dtype=np.uint32)
+        assert np.array_equal(got, want), (win, n, M)
+    # pixel -> c against the brute force
+    rng = random.Random(7)
+    for _ in range(60):
+        a, b = sorted(rng.uniform(-2.5, 2.5) for _ in range(2))
+        c, d = sorted(rng.uniform(-2.5, 2.5) for _ in range(2))
+        if b - a < 1e-3 or d - c < 1e-3:
+            continue
+        win = tuple(f32exact.to_float(f32exact.f32(v)) for v in (a, b, c, d))
+        n = rng.randint(1, 70000)
+        px, py = rng.randrange(n), rng.randrange(n)
+        want = tuple(f32exact.to_float(v) for v in f32exact.pixel_c(win, n, px, py))
+        assert orc.pixel_to_c(win, n, px, py) == want, (win, n, px, py)
+
+
+def pin_c0_pixels(orc):
+    """With the window [-1.5, 0.5] x [-1, 1] at n = 1024 the spacing is 2^-9,
+    so pixel (px, py) samples exactly c = -1.5 + px/512 + i(-1 + py/512)."""
+    for px, py in [(0, 0), (768, 512), (256, 512), (896, 512), (1023, 1023), (5, 999)]:
+        assert orc.pixel_to_c(C0_WINDOW, 1024, px, py) == (-1.5 + px / 512, -1.0 + py / 512)
+    m = orc.render_exhaustive(C0_WINDOW, 1024, 512, threads=4)
+    assert m[512, 768] == 512   # c = 0
+    assert m[512, 256] == 512   # c = -1
+    assert m[512, 896] == 512   # c = 1/4
+    assert m[512, 0] == 512     # c = -3/2
+    # c = -1.5 - i: |z_1|^2 = 3.25, z_2 = -0.25 + 2i with |z_2|^2 = 4.0625
+    assert orc.dwell(-1.5, -1.0, 512) == 2
+    assert m[0, 0] == 2
+    return m
+
+
+def pin_symmetry_and_area(orc):
+    """Conjugate symmetry (rows py and n - py of a window symmetric in Im)
+    and the area of the set, about 1.5066 (finite dwell and corner sampling
+    overestimate it a little)."""
+    n = 1024
+    m = orc.render_exhaustive(C0_WINDOW, n, 512, threads=4)
+    assert np.array_equal(m[1:], m[1:][::-1])
+    area = float((m == 512).mean()) * 4.0
+    assert 1.49 < area < 1.54, area
+    # an asymmetric spot check: c = 0.3 escapes (right of the cusp at 1/4)
+    # while c = 0.3i stays bounded
+    assert orc.dwell(0.3, 0.0, 512) < 512
+    assert orc.dwell(0.0, 0.3, 512) == 512
+
+
+def pin_no_fill_equals_exhaustive(orc):
+    """With fills disabled the recursion only rearranges per-pixel work, so
+    the map must equal the exhaustive one exactly, for any (g, r, B)."""
+    win = (-2.0, 0.6, -1.25, 1.25)
+    for n, g, r, B in [(1, 1, 2, 1), (7, 2, 2, 1), (37, 3, 2, 4), (64, 4, 2, 8),
+                       (50, 2, 3, 2), (97, 5, 4, 3)]:
+        ex = orc.render_exhaustive(win, n, 96, threads=2)
+        ms, _ = orc.render_ms(win, n, 96, g, r, B, flags=NO_FILL, threads=2)
+        assert np.array_equal(ex, ms), (n, g, r, B)
+
+
+def pin_tree_by_hand(orc):
+    """Region counts per level with fills disabled, worked out by hand from
+    the rules s0 = ceil(n/g), child side ceil(s/r), clip to the parent, drop
+    empty children, split while ceil(s/r) >= B and s > 1."""
+    win = (-2.0, 0.6, -1.25, 1.25)
+    # n=5, g=2: s0=3, regions 3x3, 2x3, 3x2, 2x2.  r=2: child side 2; the 2-wide
+    # regions keep one column of children (the second starts at the parent's
+    # end): 4 + 2 + 2 + 1 = 9 regions of side 2; then side 1: every pixel.
+    _, st = orc.render_ms(win, 5, 50, 2, 2, 1, flags=NO_FILL, threads=1)
+    assert st["regions_per_level"] == [4, 9, 25], st
+    assert st["subdivisions_per_level"] == [4, 9, 0]
+    assert st["leaves"] == 25 and st["leaf_pixels"] == 25
+    # n=8, g=2, r=4, B=2: ceil(4/4) = 1 < B, so the four initial regions are leaves.
+    _, st = orc.render_ms(win, 8, 50, 2, 4, 2, flags=NO_FILL, threads=1)
+    assert st["regions_per_level"] == [4] and st["leaves"] == 4
+    # n=7, g=3: s0=3, origins 0, 3, 6 (widths 3, 3, 1): 9 regions, then pixels.
+    _, st = orc.render_ms(win, 7, 50, 3, 3, 1, flags=NO_FILL, threads=1)
+    assert st["regions_per_level"] == [9, 49], st
+    # n=6, g=4: s0=2, origins 0, 2, 4 and one past the edge: 9 non-empty regions.
+    _, st = orc.render_ms(win, 6, 50, 4, 2, 4, flags=NO_FILL, threads=1)
+    assert st["regions_per_level"] == [9] and st["leaves"] == 9
+    # n=64, g=2, r=2, B=8: sides 32, 16, 8 then ceil(8/2)=4 < 8 -> leaves of side 8.
+    _, st = orc.render_ms(win, 64, 50, 2, 2, 8, flags=NO_FILL, threads=1)
+    assert st["regions_per_level"] == [4, 16, 64] and st["leaves"] == 64
+
+
+def _perimeter(block):
+    h, w = block.shape
+    if h <= 2 or w <= 2:
+        return block.ravel()
+    return np.concatenate([block[0], block[-1], block[1:-1, 0], block[1:-1, -1]])
+
+
+def check_region_log(ex, ms, st, log, n, g, r, B):
+    """Invariants of one Mariani-Silver run, from its region log."""
+    s0 = -(-n // g)
+    lv0 = log[log["level"] == 0]
+    cover = np.zeros((n, n), dtype=np.int32)
+    expected0 = {(x, y) for y in range(0, n, s0) for x in range(0, n, s0)}
+    assert {(int(e["x0"]), int(e["y0"])) for e in lv0} == expected0
+    for e in lv0:
+        assert e["s"] == s0 and e["w"] == min(s0, n - e["x0"]) and e["h"] == min(s0, n - e["y0"])
+    fill_px = leaf_px = 0
+    by_level = {}
+    for e in log:
+        by_level.setdefault(int(e["level"]), []).append(e)
+    for e in log:
+        x0, y0, w, h, s = int(e["x0"]), int(e["y0"]), int(e["w"]), int(e["h"]), int(e["s"])
+        assert 1 <= w <= s and 1 <= h <= s and x0 + w <= n and y0 + h <= n
+        per = _perimeter(ex[y0:y0 + h, x0:x0 + w])
+        sc = -(-s // r)
+        if e["kind"] == FILL:
+            assert np.all(per == e["dwell"])
+            assert np.all(ms[y0:y0 + h, x0:x0 + w] == e["dwell"])
+            cover[y0:y0 + h, x0:x0 + w] += 1
+            fill_px += w * h
+        elif e["kind"] == LEAF:
+            assert not np.all(per == per[0])
+            assert s == 1 or sc < B
+            assert np.array_equal(ms[y0:y0 + h, x0:x0 + w], ex[y0:y0 + h, x0:x0 + w])
+            cover[y0:y0 + h, x0:x0 + w] += 1
+            leaf_px += w * h
+        else:
+            assert e["kind"] == SUBDIVIDE
+            assert not np.all(per == per[0])
+            assert s > 1 and sc >= B
+            kids = [k for k in by_level.get(int(e["level"]) + 1, [])
+                    if x0 <= k["x0"] < x0 + w and y0 <= k["y0"] < y0 + h]
+            want = set()
+            for b in range(r):
+                for a in range(r):
+                    cx, cy = x0 + a * sc, y0 + b * sc
+                    if cx < x0 + w and cy < y0 + h:
+                        want.add((cx, cy, min(sc, x0 + w - cx), min(sc, y0 + h - cy), sc))
+            got = {(int(k["x0"]), int(k["y0"]), int(k["w"]), int(k["h"]), int(k["s"])) for k in kids}
+            assert got == want
+    assert np.all(cover == 1), "fills and leaves must tile the image exactly once"
+    assert fill_px == st["fill_pixels"] and leaf_px == st["leaf_pixels"]
+    assert fill_px + leaf_px == n * n
+    # every pixel on the perimeter of a visited region holds its own dwell
+    for e in log:
+        x0, y0, w, h = int(e["x0"]), int(e["y0"]), int(e["w"]), int(e["h"])
+        assert np.array_equal(_perimeter(ms[y0:y0 + h, x0:x0 + w]),
+                              _perimeter(ex[y0:y0 + h, x0:x0 + w]))
+
+
+def pin_ms_invariants(orc):
+    win_boundary = (-1.5, 0.5, -1.0, 1.0)
+    for n, M, g, r, B in [(64, 64, 2, 2, 8), (100, 128, 3, 2, 5), (128, 256, 4, 4, 4),
+                          (96, 200, 2, 3, 4), (250, 128, 4, 2, 16), (33, 64, 1, 2, 2)]:
+        ex = orc.render_exhaustive(win_boundary, n, M, threads=2)
+        ms, st, log = orc.render_ms(win_boundary, n, M, g, r, B, log=True)
+        check_region_log(ex, ms, st, log, n, g, r, B)
+
+
+def pin_uniform_windows(orc):
+    """Every point far outside (|c| > 2) has dwell 1 and every point of the
+    disk |c| < 1/4 lies in the main cardioid, so both windows fill at once."""
+    _, st, log = orc.render_ms((3.0, 4.0, 3.0, 4.0), 64, 100, 4, 2, 4, log=True)
+    assert st["regions_per_level"] == [16] and st["fills_per_level"] == [16]
+    assert np.all(log["dwell"] == 1)
+    ms, st = orc.render_ms((-0.15, 0.15, -0.15, 0.15), 64, 300, 4, 2, 4, threads=2)
+    assert st["fills_per_level"] == [16] and np.all(ms == 300)
+
+
+def pin_stopping_side(orc):
+    """At the n = 1024, g = 16, r = 2, B = 32 configuration the sides are 64
+    then 32, so there are two levels and every leaf has side exactly B."""
+    ex = orc.render_exhaustive(C0_WINDOW, 1024, 512, threads=4)
+    ms, st, log = orc.render_ms(C0_WINDOW, 1024, 512, 16, 2, 32, log=True)
+    assert st["levels"] == 2
+    leaves = log[log["kind"] == LEAF]
+    assert len(leaves) > 0 and np.all(leaves["s"] == 32) and np.all(leaves["level"] == 1)
+    check_region_log(ex, ms, st, log, 1024, 16, 2, 32)
+
+
+def pin_threads_and_regions(orc):
+    """Thread count changes nothing; one initial region rendered alone equals
+    its tile of the full map."""
+    win = (-2.0, 1.0, -1.5, 1.5)
+    a, sa = orc.render_ms(win, 300, 256, 5, 2, 8, threads=1)
+    b, sb = orc.render_ms(win, 300, 256, 5, 2, 8, threads=7)
+    assert np.array_equal(a, b) and sa == sb
+    it = 0
+    for gy in range(5):
+        for gx in range(5):
+            (x0, y0, w, h), tile, st = orc.render_ms_region(win, 300, 256, 5, 2, 8, gx, gy)
+            assert np.array_equal(tile, a[y0:y0 + h, x0:x0 + w])
+            it += st["iterations"]
+    assert it == sa["iterations"]
+
+
+ALL_PINS = [pin_closed_forms, pin_exact_points, pin_exact_tiny_maps,
+            pin_c0_pixels, pin_symmetry_and_area, pin_no_fill_equals_exhaustive,
+            pin_tree_by_hand, pin_ms_invariants, pin_uniform_windows, pin_stopping_side,
+            pin_threads_and_regions]
