@@ -1,0 +1,369 @@
+"""Benchmark: Mandelbrot dwell map n = 16384, dwell 2048, window
+[-1.5, 0.5] x [-1, 1] (FP32, uint32 map), rendered by ASK on GB300.
+
+One step = one ASK render of the whole map (init + one level kernel per
+subdivision depth + leaf kernel) into a preallocated 1.07 GB device map.
+Before timing, an untimed autotune picks (g, r, B) over the 75-point sweep
+g in {2..32}, r in {2, 4, 8}, B in {16..256} and then the CUDA block shape.
+
+Printed (rank 0, one JSON line): Gpixels/s of ASK (headline), dwell
+iterations per second (executed and exhaustive-equivalent), the exhaustive
+and CDP2 kernels at the same configuration, the roofline of the dominant
+kernel against the FP32 pipe, the CPU reference timed on the host cores, an
+end-to-end number through the C ABI with a host output buffer, and SM clocks
+sampled during the timed region.
+
+``--impl reference`` times the CPU reference instead (the plain C oracle,
+all host cores, a fixed sample of initial regions per step).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpixels/s and dwell-iter/s (ASK vs exhaustive vs CDP2, 1 GB300); p50/p99 latency"
+UNIT = "Gpixels/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ask", choices=["ask", "reference"])
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotune sweep")
+    ap.add_argument("--g", type=int, default=32)
+    ap.add_argument("--r", type=int, default=4)
+    ap.add_argument("--B", type=int, default=16)
+    ap.add_argument("--block", default="16x16")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas of the workload)
+# ---------------------------------------------------------------------------
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU reference (the oracle as it stands), all host cores
+# ---------------------------------------------------------------------------
+def cpu_reference_sample(C, g, r, B, seconds, seed=2206):
+    """Render seeded initial regions with the CPU reference on every host
+    core until about ``seconds`` of wall time; returns (pixels, s, cores, regions)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    from paper_2206_02255_gb300 import inputs
+    orc = oracle.default()
+    cores = oracle.default_threads()
+    order = inputs.sample_initial_regions(g, g * g, seed)
+    done_px = 0
+    used = 0
+    t0 = time.perf_counter()
+
+    def one(cell):
+        res = orc.render_ms_region(C["window"], C["n"], C["max_dwell"], g, r, B, cell[0], cell[1])
+        return 0 if res is None else res[0][2] * res[0][3]
+
+    with ThreadPoolExecutor(cores) as ex:
+        k = 0
+        while k < len(order) and time.perf_counter() - t0 < seconds:
+            batch = order[k:k + cores]
+            k += len(batch)
+            for px in ex.map(one, batch):
+                done_px += px
+            used += len(batch)
+    return done_px, time.perf_counter() - t0, cores, used
+
+
+def run_reference(args):
+    from paper_2206_02255_gb300 import inputs
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    C = inputs.C1
+    g, r, B = 32, 4, 16
+    per_step = 4.0
+    for _ in range(args.warmup):
+        cpu_reference_sample(C, g, r, B, 0.5)
+    px_total = 0
+    t_total = 0.0
+    cores = regions = 0
+    for k in range(args.steps):
+        px, t, cores, regions = cpu_reference_sample(C, g, r, B, per_step, seed=2206 + k)
+        px_total += px
+        t_total += t
+    value = px_total / t_total / 1e9
+    sample = ("%d seeded initial regions (of %dx%d) per step of n=%d, max_dwell=%d, g=%d r=%d B=%d"
+              % (regions, g, g, C["n"], C["max_dwell"], g, r, B))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": C["name"], "n": C["n"], "max_dwell": C["max_dwell"],
+                       "window": list(C["window"]), "g": g, "r": r, "B": B},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2206_02255_gb300 import ask, build, inputs
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    C = inputs.C1
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    ctx = ask.Context(local)
+    out = torch.empty((n, n), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    bx, by = (int(v) for v in args.block.split("x"))
+
+    def one(method, g, r, B, block, flags=0):
+        return ctx.render(method, win, n, M, ask.make_params(g, r, B, block, flags), out=out)
+
+    def time_renders(method, g, r, B, block, reps, flags=0):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        one(method, g, r, B, block, flags)
+        e0.record(stream)
+        for _ in range(reps):
+            one(method, g, r, B, block, flags)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # ---- untimed autotune: (g, r, B) sweep, then block shape -------------
+    tune = {"g": args.g, "r": args.r, "B": args.B, "block": [bx, by]}
+    sweep = []
+    if not args.no_tune:
+        best = None
+        for g, r, B in inputs.c1_sweep():
+            ms = time_renders("ask", g, r, B, (16, 16), 2)
+            sweep.append((g, r, B, ms))
+            if best is None or ms < best[3]:
+                best = (g, r, B, ms)
+        g, r, B = best[:3]
+        bbest = None
+        for blk in inputs.BLOCK_SHAPES:
+            ms = time_renders("ask", g, r, B, blk, 3)
+            if bbest is None or ms < bbest[1]:
+                bbest = (blk, ms)
+        tune = {"g": g, "r": r, "B": B, "block": list(bbest[0])}
+    g, r, B, blk = tune["g"], tune["r"], tune["B"], tuple(tune["block"])
+
+    # ---- counting run (untimed): algorithmic work per kernel ---------------
+    _, cst = ctx.render("ask", win, n, M, ask.make_params(g, r, B, blk, ask.FLAG_COUNT), out=out,
+                        stats=True)
+    ask_map = out.clone()
+    _, est = ctx.render("exhaustive", win, n, M, ask.make_params(g, r, B, blk, ask.FLAG_COUNT),
+                        out=out, stats=True)
+    mismatch = int((ask_map != out).sum().item())
+    del ask_map
+    launches_per_step = cst["kernel_launches"]
+
+    # ---- timed region: K ASK renders ---------------------------------------
+    for _ in range(args.warmup):
+        one("ask", g, r, B, blk)
+    ctx.timing_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one("ask", g, r, B, blk, ask.FLAG_TIMING)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = max_over_ranks(world, ms_step, dev)
+    timing = ctx.timing_read()
+
+    # ---- comparison arms at the same configuration (untimed for the headline)
+    ms_ex = time_renders("exhaustive", g, r, B, blk, max(3, args.steps // 4))
+    ms_cdp = time_renders("cdp2", g, r, B, blk, max(3, args.steps // 4))
+
+    pixels = float(n) * n
+    value = world * pixels / (ms_step / 1e3) / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    # ---- roofline of the dominant kernel (FP32 pipe) ----------------------
+    R = timing["renders"]
+    kern = {"leaf": timing["ms_leaf"] / R}
+    for i, t in enumerate(timing["ms_per_level"]):
+        kern["level%d" % i] = t / R
+    dom = max(kern, key=kern.get)
+    it_dom = cst["leaf_iterations"] if dom == "leaf" else cst["iterations_per_level"][int(dom[5:])]
+    achieved = it_dom / (kern[dom] / 1e3) / 1e9           # G dwell-iterations / s
+    f_mhz = 2070.0
+    try:
+        f_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+    except Exception:
+        pass
+    peak = sms * 128 * f_mhz * 1e6 / 6.0 / 1e9             # 6 FP32-pipe ops per iteration
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "Gdwell-iter/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 6 FP32 ops per iteration"
+                              % (sms, f_mhz)}
+    if clk and clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 6.0 / 1e9)
+
+    # ---- end to end through the C ABI with a host buffer -------------------
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((n, n), dtype=torch.int32, pin_memory=True)
+        ctx.render_host("ask", win, n, M, ask.make_params(g, r, B, blk), out=host)
+        k_e2e = max(3, args.steps // 2)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ctx.render_host("ask", win, n, M, ask.make_params(g, r, B, blk), out=host)
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        t_e2e = max_over_ranks(world, t_e2e, dev)
+        e2e = {"value": world * pixels / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(pixels * 4), "ms_per_step": 1e3 * t_e2e}
+        del host
+
+    # ---- CPU reference on a bounded sample (rank 0, N = 1) -----------------
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        px, t, cores, regions = cpu_reference_sample(C, g, r, B, 12.0)
+        cpu = {"value": px / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded initial regions of %dx%d (%d pixels) at n=%d, max_dwell=%d, "
+                         "g=%d r=%d B=%d" % (regions, g, g, px, n, M, g, r, B)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": C["name"], "n": n, "max_dwell": M, "window": list(win),
+                       "method": "ask", "g": g, "r": r, "B": B, "block": list(blk),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "output map %.2f GB > 129 MB L2, rewritten every step" % (pixels * 4 / 1e9)},
+            "dwell_iter_s": {"executed": cst["iterations"] / (ms_step / 1e3),
+                             "exhaustive_equivalent": est["iterations"] / (ms_step / 1e3)},
+            "exhaustive": {"ms": ms_ex, "gpix_s": pixels / (ms_ex / 1e3) / 1e9,
+                           "dwell_iter_s": est["iterations"] / (ms_ex / 1e3)},
+            "cdp2": {"ms": ms_cdp, "gpix_s": pixels / (ms_cdp / 1e3) / 1e9},
+            "speedup_vs_exhaustive": ms_ex / ms_step, "speedup_vs_cdp2": ms_cdp / ms_step,
+            "mismatch_vs_exhaustive_pixels": mismatch,
+            "kernels_ms": kern, "levels": cst["levels"],
+            "regions_per_level": cst["regions_per_level"], "leaves": cst["leaves"],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "tune_sweep_top5": sorted(sweep, key=lambda t: t[3])[:5],
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

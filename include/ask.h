@@ -1,0 +1,188 @@
+/*
+ * ask.h -- C ABI of the GB300 (sm_103a) Mandelbrot dwell-map library.
+ *
+ * The library computes the escape-time ("dwell") map of the Mandelbrot set
+ * over an n x n pixel window of the complex plane, three ways:
+ *
+ *   ASK_METHOD_EXHAUSTIVE  one flat kernel, one dwell per pixel
+ *                          (paper Sec. 4.1, Eq. 1-2; implementation "Ex" of
+ *                          Sec. 6.1);
+ *   ASK_METHOD_ASK         Mariani-Silver subdivision scheduled as Adaptive
+ *                          Serial Kernels: one kernel per subdivision level
+ *                          reading a device-resident offset lookup table of
+ *                          active regions and appending sub-regions to the
+ *                          next one, then one kernel for the leaf regions
+ *                          (Sec. 5, Sec. 5.2-5.3; subdivision rule Sec. 4.2.1);
+ *   ASK_METHOD_CDP2        the same subdivision with device-side child
+ *                          launches, one r x r child grid per subdividing
+ *                          region, in CUDA Dynamic Parallelism's tail-launch
+ *                          stream (the DP scheme of Sec. 3, SBR mapping of
+ *                          Sec. 4.3.1).
+ *
+ * Arithmetic (all methods, identical bits): single precision, each
+ * iteration computes zi2 = zi*zi, m = fma(zr, zr, zi2), and while m < 4
+ * updates zr' = fma(zr, zr, fma(-zi, zi, cr)), zi' = fma(zr + zr, zi, ci);
+ * the dwell is the number of updates, capped at max_dwell.  Pixel (px, py)
+ * samples c = (fma(px, dx, re_min), fma(py, dy, im_min)) with
+ * dx = (re_max - re_min) / n and dy = (im_max - im_min) / n in float.
+ *
+ * Output layout: uint32 dwell[py * n + px], row-major, py = 0 <-> im_min.
+ *
+ * Subdivision (ASK and CDP2): initial regions of side s0 = ceil(n / g);
+ * a region's perimeter (outermost rows and columns) is evaluated; a uniform
+ * perimeter fills the whole region with that dwell; otherwise, if the
+ * region's side s > 1 and ceil(s / r) >= B it splits into r x r children of
+ * side ceil(s / r), clipped to the parent, empty children dropped; else it is
+ * a leaf and every pixel is evaluated.  ASK and CDP2 produce identical maps.
+ *
+ * Errors: every entry point returns an ask_status.  Argument errors are
+ * detected before anything is launched and leave the output untouched.
+ * Errors that only the device can see (an overflowing region table, a
+ * failed device-side launch) are latched in the context and reported by the
+ * next call that synchronises: ask_render with a non-NULL stats pointer,
+ * ask_render_host, or ask_check.
+ *
+ * Threading: a context may be used by one host thread at a time; calls on
+ * one context are ordered by the stream they are given.
+ */
+#ifndef ASK_H
+#define ASK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASK_MAX_LEVELS 32
+#define ASK_MAX_N 65536u
+
+typedef enum {
+    ASK_OK = 0,
+    ASK_EINVAL = 1,        /* invalid argument (nothing launched) */
+    ASK_ENOMEM = 2,        /* device or host allocation failed */
+    ASK_ECUDA = 3,         /* a CUDA runtime call failed; see ask_last_error */
+    ASK_EOVERFLOW = 4,     /* a device-side capacity check failed */
+    ASK_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    ASK_EUNSUPPORTED = 6   /* the device is not sm_103 or lacks a feature */
+} ask_status;
+
+typedef enum {
+    ASK_METHOD_EXHAUSTIVE = 0,
+    ASK_METHOD_ASK = 1,
+    ASK_METHOD_CDP2 = 2
+} ask_method;
+
+/* flags of ask_params */
+#define ASK_FLAG_COUNT 1u   /* count dwell iterations and pixels per kind (slower) */
+#define ASK_FLAG_TIMING 2u  /* record per-kernel device times (read with ask_timing_read) */
+
+typedef struct {
+    float re_min, re_max, im_min, im_max;
+} ask_window;
+
+typedef struct {
+    uint32_t g;        /* initial grid g x g (Sec. 4.2, G = g^2) */
+    uint32_t r;        /* subdivision r x r per split (Sec. 4.2, R = r^2), >= 2 */
+    uint32_t B;        /* stop splitting below side B (Sec. 4.2.1 assumption iii) */
+    uint32_t block_x;  /* CTA shape of the per-pixel kernels; block_x * block_y */
+    uint32_t block_y;  /*   must be a multiple of 32 in [32, 1024] */
+    uint32_t flags;    /* ASK_FLAG_* */
+} ask_params;
+
+typedef struct {
+    uint32_t levels;                           /* subdivision levels run */
+    uint32_t pad_;
+    uint64_t regions_per_level[ASK_MAX_LEVELS];      /* regions evaluated at level i */
+    uint64_t fills_per_level[ASK_MAX_LEVELS];        /* uniform regions filled at level i */
+    uint64_t subdivisions_per_level[ASK_MAX_LEVELS]; /* regions split at level i */
+    uint64_t leaves;                           /* regions computed per pixel */
+    uint64_t fill_pixels;                      /* ASK_FLAG_COUNT only */
+    uint64_t leaf_pixels;                      /* ASK_FLAG_COUNT only */
+    uint64_t border_pixels;                    /* ASK_FLAG_COUNT only */
+    uint64_t iterations;                       /* ASK_FLAG_COUNT only: z-updates executed */
+    uint64_t iterations_per_level[ASK_MAX_LEVELS]; /* ASK_FLAG_COUNT, ASK: z-updates of level i */
+    uint64_t leaf_iterations;                  /* ASK_FLAG_COUNT, ASK: z-updates of the leaf kernel */
+    float ms_total;                            /* device time of the render */
+    float ms_per_level[ASK_MAX_LEVELS];        /* ASK: device time of level kernel i */
+    float ms_leaf;                             /* ASK: device time of the leaf kernel */
+    uint32_t kernel_launches;                  /* kernels this render launched from the host */
+} ask_stats;
+
+/* Per-kernel device time summed over the renders made with ASK_FLAG_TIMING
+ * since the previous ask_timing_read (at most the last 64 of them). */
+typedef struct {
+    uint32_t renders;                          /* renders summed */
+    uint32_t dropped;                          /* renders recorded but overwritten */
+    uint32_t levels;                           /* ASK: levels of the most recent render */
+    uint32_t method;                           /* method of the most recent render */
+    float ms_total;                            /* whole renders */
+    float ms_init;                             /* ASK: init kernel */
+    float ms_per_level[ASK_MAX_LEVELS];        /* ASK: level kernel i */
+    float ms_leaf;                             /* ASK: leaf kernel */
+} ask_timing;
+
+typedef struct ask_ctx ask_ctx;
+
+/* Create a context on CUDA device `device` (which becomes current).  The
+ * context owns all scratch memory (region tables, counters, and for
+ * ask_render_host a device copy of the map).  Returns ASK_EUNSUPPORTED on a
+ * device other than compute capability 10.3. */
+ask_status ask_ctx_create(ask_ctx **out, int device);
+
+/* Free everything the context owns.  NULL is ignored. */
+void ask_ctx_destroy(ask_ctx *ctx);
+
+/* Allocate the scratch that renders of size n with these parameters need,
+ * so that later ask_render calls with them allocate nothing (and may be
+ * captured into a CUDA graph).  ask_render calls this itself when needed. */
+ask_status ask_reserve(ask_ctx *ctx, ask_method method, uint32_t n,
+                       const ask_params *params);
+
+/* Render the n x n dwell map of `window` into the caller-owned device
+ * buffer d_dwell (n*n uint32, 16-byte aligned) on `stream` (a cudaStream_t;
+ * NULL = legacy default stream).  Asynchronous when stats == NULL; with a
+ * non-NULL stats pointer it synchronises the stream, fills *stats and
+ * reports latched device-side errors.  1 <= n <= 65536, max_dwell >= 1;
+ * params may be NULL for the exhaustive method (default 16 x 16 blocks). */
+ask_status ask_render(ask_ctx *ctx, ask_method method, const ask_window *window,
+                      uint32_t n, uint32_t max_dwell, const ask_params *params,
+                      uint32_t *d_dwell, void *stream, ask_stats *stats);
+
+/* Same as ask_render but the map lands in host memory h_dwell (n*n uint32,
+ * pageable or pinned): the context renders into its own device buffer and
+ * copies the result back on `stream`, then synchronises. */
+ask_status ask_render_host(ask_ctx *ctx, ask_method method, const ask_window *window,
+                           uint32_t n, uint32_t max_dwell, const ask_params *params,
+                           uint32_t *h_dwell, void *stream, ask_stats *stats);
+
+/* Synchronise `stream`, then sum the device times recorded by renders made
+ * with ASK_FLAG_TIMING since the previous call into *out and forget them.
+ * The renders must all have been issued on `stream` (or be complete). */
+ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out);
+
+/* Synchronise `stream` and return (and clear) any latched device error. */
+ask_status ask_check(ask_ctx *ctx, void *stream);
+
+/* Host-side plan of the subdivision levels for (n, g, r, B): writes the
+ * region side of each level into sides[0..*levels-1] (up to cap entries)
+ * and the maximum number of regions a level can hold into max_regions
+ * (may be NULL).  No device work. */
+ask_status ask_plan_levels(uint32_t n, uint32_t g, uint32_t r, uint32_t B,
+                           uint32_t *sides, uint64_t *max_regions, uint32_t cap,
+                           uint32_t *levels);
+
+/* Human-readable name of a status code (static storage). */
+const char *ask_status_str(ask_status status);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char *ask_last_error(const ask_ctx *ctx);
+
+/* Library version string (static storage). */
+const char *ask_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASK_H */

@@ -1,0 +1,737 @@
+// ask_api.cu -- host side of the C ABI declared in include/ask.h: argument
+// checks, the subdivision plan, scratch ownership, and the launch sequence
+// of each method.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ask_internal.h"
+
+struct ask_ctx {
+    ask::DeviceInfo dev;
+    // region tables (double buffered), leaf list, counters
+    uint2 *olt[2] = {nullptr, nullptr};
+    uint64_t olt_cap = 0;
+    uint2 *leaves = nullptr;
+    uint64_t leaf_cap = 0;
+    ask::DevCounters *ctr = nullptr;
+    ask::DevCounters *h_ctr = nullptr;  // pinned mirror for stats
+    // device map for ask_render_host
+    uint32_t *dmap = nullptr;
+    size_t dmap_elems = 0;
+    // events of the synchronous stats path: 0 = start, 1 = after init,
+    // 2 + i = after level i, levels + 2 = after the leaf kernel
+    cudaEvent_t ev[ASK_MAX_LEVELS + 3];
+    bool events = false;
+    // ASK_FLAG_TIMING: a ring of per-render event sets, read by ask_timing_read
+    struct TimingSlot {
+        cudaEvent_t ev[ASK_MAX_LEVELS + 3];
+        uint32_t levels;
+        uint32_t method;
+    };
+    static constexpr uint32_t kRing = 64;
+    TimingSlot *ring = nullptr;
+    uint64_t ring_head = 0, ring_tail = 0;
+    uint32_t ring_dropped = 0;
+    size_t cdp_pending = 0;
+    char err[256];
+};
+
+namespace ask {
+
+static uint32_t ceil_div(uint32_t a, uint32_t b) { return a / b + (a % b != 0u); }
+
+bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
+{
+    if (n == 0 || g == 0 || r < 2 || B == 0 || !plan)
+        return false;
+    std::memset(plan, 0, sizeof(*plan));
+    uint32_t s = ceil_div(n, g);
+    // multiset of interval lengths along one axis: (length, how many)
+    std::vector<std::pair<uint32_t, uint64_t>> lens;
+    const uint32_t full = n / s, rem = n % s;
+    if (full)
+        lens.push_back({s, full});
+    if (rem)
+        lens.push_back({rem, 1});
+    plan->axis0 = full + (rem ? 1u : 0u);
+    for (uint32_t i = 0;; ++i) {
+        if (i >= ASK_MAX_LEVELS)
+            return false;
+        uint64_t axis = 0;
+        for (auto &p : lens)
+            axis += p.second;
+        plan->side[i] = s;
+        plan->max_regions[i] = axis * axis;
+        if (plan->max_regions[i] >= 0xffffffffull)
+            return false;
+        const uint32_t sc = ceil_div(s, r);
+        plan->split[i] = (s > 1u && sc >= B) ? 1u : 0u;
+        plan->levels = i + 1;
+        if (!plan->split[i])
+            break;
+        std::vector<std::pair<uint32_t, uint64_t>> next;
+        auto add = [&next](uint32_t len, uint64_t cnt) {
+            for (auto &q : next)
+                if (q.first == len) {
+                    q.second += cnt;
+                    return;
+                }
+            next.push_back({len, cnt});
+        };
+        for (auto &p : lens) {
+            if (p.first / sc)
+                add(sc, (uint64_t)(p.first / sc) * p.second);
+            if (p.first % sc)
+                add(p.first % sc, p.second);
+        }
+        lens.swap(next);
+        s = sc;
+    }
+    return true;
+}
+
+}  // namespace ask
+
+using namespace ask;
+
+namespace {
+
+ask_status set_err(ask_ctx *ctx, ask_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        std::vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+ask_status cuda_err(ask_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess)
+        return ASK_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return set_err(ctx, ASK_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return set_err(ctx, ASK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool window_ok(const ask_window *w)
+{
+    return w && std::isfinite(w->re_min) && std::isfinite(w->re_max) && std::isfinite(w->im_min) &&
+           std::isfinite(w->im_max) && w->re_max > w->re_min && w->im_max > w->im_min;
+}
+
+bool block_ok(uint32_t bx, uint32_t by)
+{
+    const uint64_t t = (uint64_t)bx * by;
+    return bx >= 1 && by >= 1 && bx <= 1024 && by <= 1024 && t >= 32 && t <= 1024 && t % 32 == 0;
+}
+
+ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window, uint32_t n,
+                      uint32_t max_dwell, const ask_params *p, ask_params *eff)
+{
+    if (!ctx)
+        return ASK_EINVAL;
+    if (method != ASK_METHOD_EXHAUSTIVE && method != ASK_METHOD_ASK && method != ASK_METHOD_CDP2)
+        return set_err(ctx, ASK_EINVAL, "unknown method %d", (int)method);
+    if (!window_ok(window))
+        return set_err(ctx, ASK_EINVAL, "window must be finite with min < max");
+    if (n == 0 || n > ASK_MAX_N)
+        return set_err(ctx, ASK_EINVAL, "n must be in [1, 65536]");
+    if (max_dwell == 0 || max_dwell == 0xffffffffu)
+        return set_err(ctx, ASK_EINVAL, "max_dwell must be in [1, 2^32 - 2]");
+    ask_params d{};
+    d.g = 16;
+    d.r = 2;
+    d.B = 32;
+    d.block_x = 16;
+    d.block_y = 16;
+    d.flags = 0;
+    if (p)
+        d = *p;
+    else if (method != ASK_METHOD_EXHAUSTIVE)
+        return set_err(ctx, ASK_EINVAL, "params are required for subdivision methods");
+    if (!block_ok(d.block_x, d.block_y))
+        return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
+    if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING))
+        return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
+    if (method != ASK_METHOD_EXHAUSTIVE) {
+        if (d.g == 0 || d.g > n)
+            return set_err(ctx, ASK_EINVAL, "g must be in [1, n]");
+        if (d.r < 2 || d.r > 64)
+            return set_err(ctx, ASK_EINVAL, "r must be in [2, 64]");
+        if (d.B == 0)
+            return set_err(ctx, ASK_EINVAL, "B must be >= 1");
+    }
+    *eff = d;
+    return ASK_OK;
+}
+
+PixelMap pixel_map(const ask_window *w, uint32_t n)
+{
+    PixelMap pm;
+    pm.re_min = w->re_min;
+    pm.im_min = w->im_min;
+    // float subtraction and division, each rounded once (no contraction is
+    // possible in these expressions)
+    const float wr = w->re_max - w->re_min;
+    const float wi = w->im_max - w->im_min;
+    pm.dx = wr / (float)n;
+    pm.dy = wi / (float)n;
+    return pm;
+}
+
+ask_status ensure_counters(ask_ctx *ctx)
+{
+    if (ctx->ctr)
+        return ASK_OK;
+    cudaError_t e = cudaMalloc(&ctx->ctr, sizeof(DevCounters));
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "cudaMalloc(counters)");
+    e = cudaMemset(ctx->ctr, 0, sizeof(DevCounters));
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "cudaMemset(counters)");
+    e = cudaMallocHost(&ctx->h_ctr, sizeof(DevCounters));
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "cudaMallocHost(counters)");
+    return ASK_OK;
+}
+
+ask_status reserve_ask(ask_ctx *ctx, const LevelPlan &plan)
+{
+    uint64_t olt_need = 0;
+    for (uint32_t i = 0; i < plan.levels; ++i)
+        if (plan.max_regions[i] > olt_need)
+            olt_need = plan.max_regions[i];
+    const uint64_t leaf_need = plan.max_regions[plan.levels - 1];
+    if (olt_need > ctx->olt_cap) {
+        for (int b = 0; b < 2; ++b) {
+            if (ctx->olt[b])
+                cudaFree(ctx->olt[b]);
+            ctx->olt[b] = nullptr;
+        }
+        ctx->olt_cap = 0;
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t e = cudaMalloc(&ctx->olt[b], olt_need * sizeof(uint2));
+            if (e != cudaSuccess)
+                return cuda_err(ctx, e, "cudaMalloc(region table)");
+        }
+        ctx->olt_cap = olt_need;
+    }
+    if (leaf_need > ctx->leaf_cap) {
+        if (ctx->leaves)
+            cudaFree(ctx->leaves);
+        ctx->leaves = nullptr;
+        ctx->leaf_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->leaves, leaf_need * sizeof(uint2));
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaMalloc(leaf list)");
+        ctx->leaf_cap = leaf_need;
+    }
+    return ensure_counters(ctx);
+}
+
+ask_status ensure_events(ask_ctx *ctx)
+{
+    if (ctx->events)
+        return ASK_OK;
+    for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i) {
+        cudaError_t e = cudaEventCreate(&ctx->ev[i]);
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaEventCreate");
+    }
+    ctx->events = true;
+    return ASK_OK;
+}
+
+ask_status latched_error(ask_ctx *ctx, uint32_t err)
+{
+    if (err & ERR_DEVICE_LAUNCH)
+        return set_err(ctx, ASK_ECUDA, "a device-side child launch failed (pending-launch limit?)");
+    if (err & (ERR_OLT_OVERFLOW | ERR_LEAF_OVERFLOW))
+        return set_err(ctx, ASK_EOVERFLOW, "a region table overflowed its capacity");
+    if (err)
+        return set_err(ctx, ASK_EOVERFLOW, "device error bits 0x%x", err);
+    return ASK_OK;
+}
+
+// Copy counters back (the stream is synchronised), clear the latched error.
+ask_status read_counters(ask_ctx *ctx, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(ctx->h_ctr, ctx->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "reading device counters");
+    const uint32_t err = ctx->h_ctr->error;
+    if (err) {
+        e = cudaMemsetAsync(&ctx->ctr->error, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "clearing the device error word");
+    }
+    return latched_error(ctx, err);
+}
+
+ask_status ensure_ring(ask_ctx *ctx)
+{
+    if (ctx->ring)
+        return ASK_OK;
+    ask_ctx::TimingSlot *ring = new (std::nothrow) ask_ctx::TimingSlot[ask_ctx::kRing];
+    if (!ring)
+        return set_err(ctx, ASK_ENOMEM, "timing ring");
+    for (uint32_t k = 0; k < ask_ctx::kRing; ++k) {
+        ring[k].levels = 0;
+        ring[k].method = 0;
+        for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i) {
+            cudaError_t e = cudaEventCreate(&ring[k].ev[i]);
+            if (e != cudaSuccess) {
+                delete[] ring;
+                return cuda_err(ctx, e, "cudaEventCreate");
+            }
+        }
+    }
+    ctx->ring = ring;
+    return ASK_OK;
+}
+
+// Event marks of one render: the stats events and/or a timing-ring slot.
+struct Marks {
+    cudaEvent_t *st = nullptr;
+    cudaEvent_t *tm = nullptr;
+    void at(int k, cudaStream_t s) const
+    {
+        if (st)
+            cudaEventRecord(st[k], s);
+        if (tm)
+            cudaEventRecord(tm[k], s);
+    }
+};
+
+ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window, uint32_t n,
+                       uint32_t max_dwell, const ask_params &p, uint32_t *d_dwell, cudaStream_t s,
+                       ask_stats *stats)
+{
+    const bool count = (p.flags & ASK_FLAG_COUNT) != 0;
+    const bool timing = (p.flags & ASK_FLAG_TIMING) != 0;
+    const PixelMap pm = pixel_map(window, n);
+    ask_status st;
+    cudaError_t e;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        if ((st = ensure_events(ctx)) != ASK_OK)
+            return st;
+    }
+    if (timing && (st = ensure_ring(ctx)) != ASK_OK)
+        return st;
+    if ((st = ensure_counters(ctx)) != ASK_OK)
+        return st;
+    Marks mk;
+    if (stats)
+        mk.st = ctx->ev;
+    ask_ctx::TimingSlot *slot = nullptr;
+    if (timing) {
+        if (ctx->ring_head - ctx->ring_tail == ask_ctx::kRing) {
+            ++ctx->ring_tail;  // the oldest unread render is overwritten
+            ++ctx->ring_dropped;
+        }
+        slot = &ctx->ring[ctx->ring_head % ask_ctx::kRing];
+        slot->method = (uint32_t)method;
+        slot->levels = 0;
+        mk.tm = slot->ev;
+    }
+    uint32_t launches = 0;
+
+    if (method == ASK_METHOD_EXHAUSTIVE) {
+        mk.at(0, s);
+        if (count) {
+            if ((e = launch_init(nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
+                return cuda_err(ctx, e, "init kernel");
+            ++launches;
+        }
+        if ((e = launch_exhaustive(d_dwell, n, pm, max_dwell, p.block_x, p.block_y, count, ctx->ctr, s)) !=
+            cudaSuccess)
+            return cuda_err(ctx, e, "exhaustive kernel");
+        ++launches;
+        mk.at(1, s);
+        if (timing)
+            ++ctx->ring_head;
+        if (stats) {
+            if ((st = read_counters(ctx, s)) != ASK_OK)
+                return st;
+            cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[1]);
+            stats->iterations = count ? ctx->h_ctr->iterations : 0;
+            stats->kernel_launches = launches;
+        }
+        return ASK_OK;
+    }
+
+    LevelPlan plan;
+    if (!make_plan(n, p.g, p.r, p.B, &plan))
+        return set_err(ctx, ASK_EINVAL, "no valid subdivision plan for n=%u g=%u r=%u B=%u", n, p.g, p.r, p.B);
+
+    if (method == ASK_METHOD_CDP2) {
+        if (plan.levels > 23)
+            return set_err(ctx, ASK_EINVAL, "CDP2 nesting would exceed the device runtime's depth limit");
+        // At most one pending launch per subdividing region of a level.  The
+        // limit is set generously on first use; raising it later may be
+        // refused once device-runtime kernels have run, in which case the old
+        // limit stays and a device launch that exceeds it is latched as an
+        // error (never a hang or a fault).
+        uint64_t need = 1u << 18;
+        for (uint32_t i = 0; i < plan.levels; ++i)
+            if (plan.split[i] && plan.max_regions[i] > need)
+                need = plan.max_regions[i];
+        if (need > (1u << 22))
+            need = 1u << 22;
+        if (need > ctx->cdp_pending) {
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return cuda_err(ctx, e, "cudaStreamSynchronize");
+            if (cdp2_set_pending_limit((size_t)need) == cudaSuccess)
+                ctx->cdp_pending = (size_t)need;
+            else if (ctx->cdp_pending == 0)
+                return set_err(ctx, ASK_EUNSUPPORTED, "cannot set the device runtime's pending-launch limit");
+            cudaGetLastError();  // a refused raise is not sticky
+        }
+        mk.at(0, s);
+        if ((e = launch_init(nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "init kernel");
+        CdpArgs a;
+        a.map = d_dwell;
+        a.n = n;
+        a.pm = pm;
+        a.max_dwell = max_dwell;
+        a.r = p.r;
+        a.B = p.B;
+        a.count = count ? 1u : 0u;
+        a.ctr = ctx->ctr;
+        if ((e = launch_cdp2(a, p.g, plan.side[0], p.block_x, p.block_y, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "CDP2 root kernel");
+        launches = 2;
+        mk.at(1, s);
+        if (timing)
+            ++ctx->ring_head;
+        if (stats) {
+            if ((st = read_counters(ctx, s)) != ASK_OK)
+                return st;
+            cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[1]);
+            const DevCounters &c = *ctx->h_ctr;
+            stats->levels = plan.levels;
+            for (uint32_t i = 0; i < plan.levels; ++i) {
+                stats->fills_per_level[i] = c.fills[i];
+                stats->subdivisions_per_level[i] = c.subdivs[i];
+            }
+            stats->leaves = c.leaf_count;
+            stats->iterations = c.iterations;
+            stats->kernel_launches = launches;
+        }
+        return ASK_OK;
+    }
+
+    // ---- ASK: init, one level kernel per depth, leaf kernel ---------------
+    if ((st = reserve_ask(ctx, plan)) != ASK_OK)
+        return st;
+    const int sms = ctx->dev.sms;
+    const uint32_t L = plan.levels;
+    mk.at(0, s);
+    if ((e = launch_init(ctx->olt[0], ctx->ctr, n, plan.side[0], plan.axis0, s)) != cudaSuccess)
+        return cuda_err(ctx, e, "init kernel");
+    ++launches;
+    mk.at(1, s);
+    for (uint32_t i = 0; i < L; ++i) {
+        LevelArgs a;
+        a.map = d_dwell;
+        a.n = n;
+        a.pm = pm;
+        a.max_dwell = max_dwell;
+        a.level = i;
+        a.side = plan.side[i];
+        a.split = plan.split[i];
+        a.child_side = ceil_div(plan.side[i], p.r);
+        a.r = p.r;
+        a.olt_in = ctx->olt[i & 1];
+        a.olt_out = ctx->olt[(i + 1) & 1];
+        a.olt_cap = (uint32_t)ctx->olt_cap;
+        a.leaves = ctx->leaves;
+        a.leaf_cap = (uint32_t)ctx->leaf_cap;
+        a.ctr = ctx->ctr;
+        // one CTA per region while a level holds too few regions to give
+        // every SM several warps, one warp per region below that
+        const uint64_t warp_slots = (uint64_t)sms * 16u;
+        const int mode = (plan.max_regions[i] < warp_slots && plan.side[i] >= 64u) ? 1 : 0;
+        const uint32_t threads = plan.side[i] >= 1024u ? 512u : 256u;
+        if ((e = launch_level(a, mode, threads, count, sms, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "level kernel");
+        ++launches;
+        mk.at(2 + (int)i, s);
+    }
+    LeafArgs la;
+    la.map = d_dwell;
+    la.n = n;
+    la.pm = pm;
+    la.max_dwell = max_dwell;
+    la.side = plan.side[L - 1];
+    la.leaves = ctx->leaves;
+    la.leaf_cap = (uint32_t)ctx->leaf_cap;
+    la.ctr = ctx->ctr;
+    if ((e = launch_leaf(la, p.block_x, p.block_y, count, sms, s)) != cudaSuccess)
+        return cuda_err(ctx, e, "leaf kernel");
+    ++launches;
+    mk.at(2 + (int)L, s);
+    if (timing) {
+        slot->levels = L;
+        ++ctx->ring_head;
+    }
+    if (stats) {
+        if ((st = read_counters(ctx, s)) != ASK_OK)
+            return st;
+        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[L + 2]);
+        for (uint32_t i = 0; i < L; ++i)
+            cudaEventElapsedTime(&stats->ms_per_level[i], ctx->ev[i + 1], ctx->ev[i + 2]);
+        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 1], ctx->ev[L + 2]);
+        const DevCounters &c = *ctx->h_ctr;
+        stats->levels = L;
+        for (uint32_t i = 0; i < L; ++i) {
+            stats->regions_per_level[i] = c.count[i];
+            stats->fills_per_level[i] = c.fills[i];
+            stats->subdivisions_per_level[i] = c.subdivs[i];
+            stats->iterations_per_level[i] = c.level_iters[i];
+        }
+        stats->leaves = c.leaf_count;
+        stats->fill_pixels = c.fill_pixels;
+        stats->leaf_pixels = c.leaf_pixels;
+        stats->border_pixels = c.border_pixels;
+        stats->iterations = c.iterations;
+        stats->leaf_iterations = c.leaf_iters;
+        stats->kernel_launches = launches;
+    }
+    return ASK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ask_version(void) { return "ask-gb300 0.1 (sm_103a)"; }
+
+const char *ask_status_str(ask_status s)
+{
+    switch (s) {
+    case ASK_OK: return "ok";
+    case ASK_EINVAL: return "invalid argument";
+    case ASK_ENOMEM: return "out of memory";
+    case ASK_ECUDA: return "CUDA error";
+    case ASK_EOVERFLOW: return "device capacity overflow";
+    case ASK_ETIMEOUT: return "device wait timed out";
+    case ASK_EUNSUPPORTED: return "unsupported device";
+    }
+    return "unknown status";
+}
+
+const char *ask_last_error(const ask_ctx *ctx) { return ctx ? ctx->err : ""; }
+
+ask_status ask_ctx_create(ask_ctx **out, int device)
+{
+    if (!out)
+        return ASK_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0 || device < 0 || device >= ndev)
+        return ASK_EUNSUPPORTED;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return ASK_ECUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return ASK_ECUDA;
+    if (!(prop.major == 10 && prop.minor == 3))
+        return ASK_EUNSUPPORTED;  // the library is built for sm_103a only
+    ask_ctx *ctx = new (std::nothrow) ask_ctx();
+    if (!ctx)
+        return ASK_ENOMEM;
+    ctx->err[0] = 0;
+    ctx->dev.device = device;
+    ctx->dev.sms = prop.multiProcessorCount;
+    ctx->dev.cc_major = prop.major;
+    ctx->dev.cc_minor = prop.minor;
+    *out = ctx;
+    return ASK_OK;
+}
+
+void ask_ctx_destroy(ask_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->dev.device);
+    for (int b = 0; b < 2; ++b)
+        if (ctx->olt[b])
+            cudaFree(ctx->olt[b]);
+    if (ctx->leaves)
+        cudaFree(ctx->leaves);
+    if (ctx->ctr)
+        cudaFree(ctx->ctr);
+    if (ctx->h_ctr)
+        cudaFreeHost(ctx->h_ctr);
+    if (ctx->dmap)
+        cudaFree(ctx->dmap);
+    if (ctx->events)
+        for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i)
+            cudaEventDestroy(ctx->ev[i]);
+    if (ctx->ring) {
+        for (uint32_t k = 0; k < ask_ctx::kRing; ++k)
+            for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i)
+                cudaEventDestroy(ctx->ring[k].ev[i]);
+        delete[] ctx->ring;
+    }
+    delete ctx;
+}
+
+ask_status ask_plan_levels(uint32_t n, uint32_t g, uint32_t r, uint32_t B, uint32_t *sides,
+                           uint64_t *max_regions, uint32_t cap, uint32_t *levels)
+{
+    if (!levels || n == 0 || n > ASK_MAX_N || g == 0 || g > n || r < 2 || r > 64 || B == 0)
+        return ASK_EINVAL;
+    LevelPlan plan;
+    if (!make_plan(n, g, r, B, &plan))
+        return ASK_EINVAL;
+    *levels = plan.levels;
+    for (uint32_t i = 0; i < plan.levels && i < cap; ++i) {
+        if (sides)
+            sides[i] = plan.side[i];
+        if (max_regions)
+            max_regions[i] = plan.max_regions[i];
+    }
+    return ASK_OK;
+}
+
+ask_status ask_reserve(ask_ctx *ctx, ask_method method, uint32_t n, const ask_params *params)
+{
+    if (!ctx)
+        return ASK_EINVAL;
+    const ask_window w = {-2.0f, 1.0f, -1.5f, 1.5f};
+    ask_params eff;
+    ask_status st = check_args(ctx, method, &w, n, 1, params, &eff);
+    if (st != ASK_OK)
+        return st;
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    if (method != ASK_METHOD_ASK)
+        return ensure_counters(ctx);
+    LevelPlan plan;
+    if (!make_plan(n, eff.g, eff.r, eff.B, &plan))
+        return set_err(ctx, ASK_EINVAL, "no valid subdivision plan");
+    return reserve_ask(ctx, plan);
+}
+
+ask_status ask_render(ask_ctx *ctx, ask_method method, const ask_window *window, uint32_t n,
+                      uint32_t max_dwell, const ask_params *params, uint32_t *d_dwell, void *stream,
+                      ask_stats *stats)
+{
+    ask_params eff;
+    ask_status st = check_args(ctx, method, window, n, max_dwell, params, &eff);
+    if (st != ASK_OK)
+        return st;
+    if (!d_dwell || ((uintptr_t)d_dwell & 15u))
+        return set_err(ctx, ASK_EINVAL, "d_dwell must be a non-NULL 16-byte aligned device pointer");
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    return render_impl(ctx, method, window, n, max_dwell, eff, d_dwell, (cudaStream_t)stream, stats);
+}
+
+ask_status ask_render_host(ask_ctx *ctx, ask_method method, const ask_window *window, uint32_t n,
+                           uint32_t max_dwell, const ask_params *params, uint32_t *h_dwell,
+                           void *stream, ask_stats *stats)
+{
+    ask_params eff;
+    ask_status st = check_args(ctx, method, window, n, max_dwell, params, &eff);
+    if (st != ASK_OK)
+        return st;
+    if (!h_dwell)
+        return set_err(ctx, ASK_EINVAL, "h_dwell must be non-NULL");
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    const size_t elems = (size_t)n * n;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (elems > ctx->dmap_elems) {
+        if (ctx->dmap) {
+            cudaStreamSynchronize(s);
+            cudaFree(ctx->dmap);
+        }
+        ctx->dmap = nullptr;
+        ctx->dmap_elems = 0;
+        cudaError_t e = cudaMalloc(&ctx->dmap, elems * sizeof(uint32_t));
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaMalloc(device map)");
+        ctx->dmap_elems = elems;
+    }
+    st = render_impl(ctx, method, window, n, max_dwell, eff, ctx->dmap, s, stats);
+    if (st != ASK_OK)
+        return st;
+    cudaError_t e = cudaMemcpyAsync(h_dwell, ctx->dmap, elems * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "copying the map to the host");
+    if (!stats)
+        return read_counters(ctx, s);  // report latched device errors
+    return ASK_OK;
+}
+
+ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
+{
+    if (!ctx || !out)
+        return ASK_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "cudaStreamSynchronize");
+    out->dropped = ctx->ring_dropped;
+    for (uint64_t k = ctx->ring_tail; k < ctx->ring_head; ++k) {
+        const ask_ctx::TimingSlot &sl = ctx->ring[k % ask_ctx::kRing];
+        const uint32_t L = sl.levels;
+        const int last = (sl.method == ASK_METHOD_ASK) ? (int)L + 2 : 1;
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[last])) != cudaSuccess)
+            return cuda_err(ctx, e, "cudaEventElapsedTime");
+        out->ms_total += ms;
+        if (sl.method == ASK_METHOD_ASK) {
+            cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[1]);
+            out->ms_init += ms;
+            for (uint32_t i = 0; i < L; ++i) {
+                cudaEventElapsedTime(&ms, sl.ev[i + 1], sl.ev[i + 2]);
+                out->ms_per_level[i] += ms;
+            }
+            cudaEventElapsedTime(&ms, sl.ev[L + 1], sl.ev[L + 2]);
+            out->ms_leaf += ms;
+        }
+        out->levels = L;
+        out->method = sl.method;
+        ++out->renders;
+    }
+    ctx->ring_tail = ctx->ring_head;
+    ctx->ring_dropped = 0;
+    return ASK_OK;
+}
+
+ask_status ask_check(ask_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return ASK_EINVAL;
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    ask_status st = ensure_counters(ctx);
+    if (st != ASK_OK)
+        return st;
+    return read_counters(ctx, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// ask_cdp2.cu -- Mariani-Silver subdivision driven by CUDA Dynamic
+// Parallelism (paper Sec. 3; the DP implementations compared in Sec. 6),
+// written for the CDP2 device runtime of CUDA 12+: a subdividing region
+// launches one child grid, r x r CTAs (one per non-empty sub-region, the SBR
+// mapping of Sec. 4.3.1), into the tail-launch stream, so no parent ever
+// waits on a child.  The host sees the render complete when the whole tree
+// of grids has completed.
+//
+// This translation unit is compiled with relocatable device code and linked
+// against the device runtime; the rest of the library is not.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ask_device.cuh"
+#include "ask_internal.h"
+
+namespace ask {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kStageMax = 16384;  // staged perimeter pixels per CTA
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// One CTA = one region: child (blockIdx.x, blockIdx.y) of side `side` inside
+// the parent rectangle (px0, py0, pw, ph).  The root grid's "parent" is the
+// whole image and its children are the g x g initial regions.
+__global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t px0, uint32_t py0,
+                                                           uint32_t pw, uint32_t ph, uint32_t side,
+                                                           uint32_t level)
+{
+    extern __shared__ uint32_t stage[];
+    __shared__ uint32_t red_min[32], red_max[32];
+    __shared__ uint32_t s_min, s_max;
+
+    const uint32_t x0 = px0 + blockIdx.x * side, y0 = py0 + blockIdx.y * side;
+    if (x0 >= px0 + pw || y0 >= py0 + ph)
+        return;  // empty child (uniform over the CTA)
+    Region g;
+    g.x0 = x0;
+    g.y0 = y0;
+    g.w = min(side, px0 + pw - x0);
+    g.h = min(side, py0 + ph - y0);
+
+    const uint32_t T = blockDim.x * blockDim.y;
+    const uint32_t tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const uint32_t lane = tid & 31u, wid = tid >> 5, nw = T >> 5;
+    const uint32_t stage_cap = min(4u * side, kStageMax);
+    unsigned long long it = 0;
+
+    // exploration query: perimeter dwells, staged in shared memory
+    const uint32_t P = perimeter_size(g.w, g.h);
+    uint32_t dmin = 0xffffffffu, dmax = 0u;
+    for (uint32_t k = tid; k < P; k += T) {
+        uint32_t px, py;
+        perimeter_pixel(g, k, px, py);
+        const float2 c = pixel_c(a.pm, px, py);
+        const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+        dmin = min(dmin, d);
+        dmax = max(dmax, d);
+        if (k < stage_cap)
+            stage[k] = d;
+        else
+            a.map[(size_t)py * a.n + px] = d;
+        it += d;
+    }
+    dmin = __reduce_min_sync(kFull, dmin);
+    dmax = __reduce_max_sync(kFull, dmax);
+    if (lane == 0) {
+        red_min[wid] = dmin;
+        red_max[wid] = dmax;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
+        uint32_t m1 = lane < nw ? red_max[lane] : 0u;
+        m0 = __reduce_min_sync(kFull, m0);
+        m1 = __reduce_max_sync(kFull, m1);
+        if (lane == 0) {
+            s_min = m0;
+            s_max = m1;
+        }
+    }
+    __syncthreads();
+    dmin = s_min;
+    dmax = s_max;
+
+    if (dmin == dmax) {
+        fill_rect(a.map, a.n, g, dmin, tid, T);
+        if (tid == 0)
+            atomicAdd(&a.ctr->fills[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
+    } else {
+        const uint32_t sc = ceil_div_u32(side, a.r);
+        if (side > 1u && sc >= a.B) {
+            if (tid == 0) {
+                atomicAdd(&a.ctr->subdivs[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
+                const uint32_t cx = min(a.r, ceil_div_u32(g.w, sc));
+                const uint32_t cy = min(a.r, ceil_div_u32(g.h, sc));
+                const size_t smem = (size_t)min(4u * sc, kStageMax) * sizeof(uint32_t);
+                cdp2_region_kernel<<<dim3(cx, cy), dim3(blockDim.x, blockDim.y), smem,
+                                     cudaStreamTailLaunch>>>(a, g.x0, g.y0, g.w, g.h, sc,
+                                                             level + 1u);
+                if (cudaGetLastError() != cudaSuccess)
+                    atomicOr(&a.ctr->error, ERR_DEVICE_LAUNCH);
+            }
+        } else {
+            // leaf: perimeter from the stage, interior pixel by pixel
+            const uint32_t staged = min(P, stage_cap);
+            for (uint32_t k = tid; k < staged; k += T) {
+                uint32_t px, py;
+                perimeter_pixel(g, k, px, py);
+                a.map[(size_t)py * a.n + px] = stage[k];
+            }
+            for (uint32_t ty0 = 0; ty0 < g.h; ty0 += blockDim.y) {
+                for (uint32_t tx0 = 0; tx0 < g.w; tx0 += blockDim.x) {
+                    const uint32_t px = g.x0 + tx0 + threadIdx.x, py = g.y0 + ty0 + threadIdx.y;
+                    if (px < g.x0 + g.w && py < g.y0 + g.h && !on_perimeter(g, px, py)) {
+                        const float2 c = pixel_c(a.pm, px, py);
+                        const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+                        a.map[(size_t)py * a.n + px] = d;
+                        it += d;
+                    }
+                }
+            }
+            if (tid == 0)
+                atomicAdd(&a.ctr->leaf_count, 1u);
+        }
+    }
+    if (a.count) {
+        it = warp_sum_u64(it);
+        if (lane == 0 && it)
+            atomicAdd(&a.ctr->iterations, it);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, uint32_t by,
+                        cudaStream_t s)
+{
+    const uint32_t axis0 = (a.n + s0 - 1) / s0;  // non-empty initial regions per axis
+    (void)g;
+    const size_t smem = (size_t)min(4u * s0, kStageMax) * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(cdp2_region_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kStageMax * sizeof(uint32_t)));
+    cdp2_region_kernel<<<dim3(axis0, axis0), dim3(bx, by), smem, s>>>(a, 0u, 0u, a.n, a.n, s0, 0u);
+    return cudaGetLastError();
+}
+
+cudaError_t cdp2_set_pending_limit(size_t launches)
+{
+    return cudaDeviceSetLimit(cudaLimitDevRuntimePendingLaunchCount, launches);
+}
+
+}  // namespace ask

@@ -1,0 +1,115 @@
+// ask_internal.h -- declarations shared by the library's translation units
+// (host driver, ASK/exhaustive kernels, CDP2 kernels).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ask.h"
+
+namespace ask {
+
+// Pixel -> c mapping, computed on the host once per render:
+// cr = fma(px, dx, re_min), ci = fma(py, dy, im_min).
+struct PixelMap {
+    float re_min, im_min, dx, dy;
+};
+
+// Device-resident counters of one render.  Zeroed by the init kernel.
+struct DevCounters {
+    uint32_t count[ASK_MAX_LEVELS + 1];     // entries in the region table of level i
+    uint32_t fills[ASK_MAX_LEVELS];         // uniform regions filled at level i
+    uint32_t subdivs[ASK_MAX_LEVELS];       // regions split at level i
+    uint32_t leaf_count;                    // entries in the leaf list
+    uint32_t error;                         // ERR_* bits, latched
+    unsigned long long iterations;          // COUNT mode: z-updates
+    unsigned long long fill_pixels;         // COUNT mode
+    unsigned long long leaf_pixels;         // COUNT mode
+    unsigned long long border_pixels;       // COUNT mode
+    unsigned long long level_iters[ASK_MAX_LEVELS];  // COUNT mode: z-updates of level i
+    unsigned long long leaf_iters;          // COUNT mode: z-updates of the leaf kernel
+};
+
+enum : uint32_t {
+    ERR_OLT_OVERFLOW = 1u,
+    ERR_LEAF_OVERFLOW = 2u,
+    ERR_DEVICE_LAUNCH = 4u,
+    ERR_DEPTH = 8u,
+};
+
+// One level of the subdivision plan.
+struct LevelPlan {
+    uint32_t levels;                        // number of level kernels
+    uint32_t side[ASK_MAX_LEVELS];          // nominal region side at level i
+    uint32_t split[ASK_MAX_LEVELS];         // 1 if non-uniform regions of level i split
+    uint64_t max_regions[ASK_MAX_LEVELS];   // upper bound on regions at level i
+    uint32_t axis0;                         // non-empty initial regions per axis
+};
+
+// Fills `plan`; returns false if the parameters are invalid or a level could
+// hold 2^32 regions or more.
+bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan);
+
+// Launch configuration chosen per device at context creation.
+struct DeviceInfo {
+    int device;
+    int sms;
+    int cc_major, cc_minor;
+};
+
+// ---- kernels of ask_kernels.cu -------------------------------------------
+cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t max_dwell,
+                              uint32_t bx, uint32_t by, bool count, DevCounters *ctr,
+                              cudaStream_t s);
+cudaError_t launch_init(uint2 *olt0, DevCounters *ctr, uint32_t n, uint32_t s0,
+                        uint32_t axis0, cudaStream_t s);
+
+struct LevelArgs {
+    uint32_t *map;
+    uint32_t n;
+    PixelMap pm;
+    uint32_t max_dwell;
+    uint32_t level;
+    uint32_t side;        // nominal side of this level's regions
+    uint32_t split;       // non-uniform regions split (else become leaves)
+    uint32_t child_side;  // ceil(side / r)
+    uint32_t r;
+    const uint2 *olt_in;
+    uint2 *olt_out;
+    uint32_t olt_cap;     // capacity of olt_out
+    uint2 *leaves;
+    uint32_t leaf_cap;
+    DevCounters *ctr;
+};
+// mode: 0 = one warp per region, 1 = one CTA of `threads` per region
+cudaError_t launch_level(const LevelArgs &a, int mode, uint32_t threads, bool count,
+                         int sms, cudaStream_t s);
+
+struct LeafArgs {
+    uint32_t *map;
+    uint32_t n;
+    PixelMap pm;
+    uint32_t max_dwell;
+    uint32_t side;        // nominal side of the leaf regions
+    const uint2 *leaves;
+    uint32_t leaf_cap;    // capacity of the leaf list
+    DevCounters *ctr;
+};
+cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, int sms,
+                        cudaStream_t s);
+
+// ---- kernels of ask_cdp2.cu ----------------------------------------------
+struct CdpArgs {
+    uint32_t *map;
+    uint32_t n;
+    PixelMap pm;
+    uint32_t max_dwell;
+    uint32_t r, B;
+    uint32_t count;       // ASK_FLAG_COUNT
+    DevCounters *ctr;
+};
+cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, uint32_t by,
+                        cudaStream_t s);
+cudaError_t cdp2_set_pending_limit(size_t launches);
+
+}  // namespace ask

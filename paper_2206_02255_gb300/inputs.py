@@ -1,0 +1,64 @@
+"""Workload definitions and seeded input generators.
+
+Shared by the GPU path's tests and benchmark and by the CPU reference's
+checks.  It holds no part of the method's arithmetic: only windows of the
+complex plane, sizes, dwell caps, subdivision parameters and seeded samples
+of them.
+
+The paper measures on the Mandelbrot set over a fixed window with dwell 512
+for n from 1024 up to 65536 (Sec. 6.1) and sweeps g, r, B and the CUDA block
+shape (Sec. 6.2, Table 2, Fig. 6).  The configurations below follow that
+recipe at three sizes.
+"""
+import itertools
+import random
+
+# Window corners as (re_min, re_max, im_min, im_max).  The paper's
+# "[-1.5, -1] x [0.5, 1]" is read as the corners (-1.5, -1) and (0.5, 1).
+WINDOW_PAPER = (-1.5, 0.5, -1.0, 1.0)
+WINDOW_WIDE = (-2.0, 1.0, -1.5, 1.5)
+
+# n = 1024, dwell 512: the small case the CPU reference renders in seconds.
+C0 = dict(name="mandelbrot_n1024_d512", window=WINDOW_PAPER, n=1024, max_dwell=512,
+          g=16, r=2, B=32)
+# n = 16384, dwell 2048: the measured configuration, with its g, r, B sweep.
+C1 = dict(name="mandelbrot_n16384_d2048", window=WINDOW_PAPER, n=16384, max_dwell=2048)
+C1_G = (2, 4, 8, 16, 32)
+C1_R = (2, 4, 8)
+C1_B = (16, 32, 64, 128, 256)
+# n = 65536, dwell 4096 (a 17.2 GB uint32 map).
+C2 = dict(name="mandelbrot_n65536_d4096", window=WINDOW_WIDE, n=65536, max_dwell=4096)
+
+# CUDA block shapes explored by the paper (Sec. 6.2, Table 2).
+BLOCK_SHAPES = ((8, 8), (16, 16), (32, 32), (64, 4), (64, 8))
+
+
+def c1_sweep():
+    """The 75 (g, r, B) points of the n = 16384 sweep."""
+    return list(itertools.product(C1_G, C1_R, C1_B))
+
+
+def sample_initial_regions(g, k, seed):
+    """k distinct initial-region indices (gx, gy) of a g x g grid, seeded."""
+    rng = random.Random(seed)
+    cells = [(gx, gy) for gy in range(g) for gx in range(g)]
+    return rng.sample(cells, min(k, len(cells)))
+
+
+def sample_pixels(n, k, seed):
+    """k seeded pixel coordinates (px, py) in [0, n)^2."""
+    rng = random.Random(seed)
+    return [(rng.randrange(n), rng.randrange(n)) for _ in range(k)]
+
+
+def random_windows(k, seed, span=(1e-3, 3.0)):
+    """k seeded windows inside [-2.2, 1.2] x [-1.6, 1.6] with sides in span."""
+    rng = random.Random(seed)
+    out = []
+    for _ in range(k):
+        wr = rng.uniform(*span)
+        wi = rng.uniform(*span)
+        re0 = rng.uniform(-2.2, 1.2 - wr) if wr < 3.4 else -2.2
+        im0 = rng.uniform(-1.6, 1.6 - wi) if wi < 3.2 else -1.6
+        out.append((re0, re0 + wr, im0, im0 + wi))
+    return out

@@ -4,16 +4,50 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-if ROOT not in sys.path:
-    sys.path.insert(0, ROOT)
+TESTS = os.path.dirname(os.path.abspath(__file__))
+for p in (ROOT, TESTS):
+    if p not in sys.path:
+        sys.path.insert(0, p)
 
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: minutes-long GPU parity cases at full size")
+    config.addinivalue_line("markers", "slow: full-size GPU cases (n = 16384 and 65536)")
+
+
+def _have_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def pytest_collection_modifyitems(config, items):
+    if _have_gpu():
+        return
+    skip = pytest.mark.skip(reason="no CUDA device in this process")
+    for item in items:
+        if "gpu" in item.keywords:
+            item.add_marker(skip)
 
 
 @pytest.fixture(scope="session")
 def orc():
     import oracle
     return oracle.default()
+
+
+@pytest.fixture(scope="session")
+def asklib():
+    """The CUDA library, built in-tree if needed (a failed build fails)."""
+    from paper_2206_02255_gb300 import ask, build
+    build.build()
+    return ask
+
+
+@pytest.fixture(scope="session")
+def ctx(asklib):
+    c = asklib.Context(0)
+    yield c
+    c.close()

@@ -1,0 +1,337 @@
+"""GPU parity: every method's dwell map against the CPU reference, bit for
+bit, through the C ABI (``libask.so`` via the ctypes binding).
+
+* exhaustive kernel  == reference per-pixel map (Sec. 4.1);
+* ASK and CDP2       == reference serial Mariani-Silver (Sec. 4.2.1, Sec. 5),
+  including the per-level region, fill and split counts;
+* tiny grids with every small (g, r, B), ragged sizes, all block shapes;
+* full-size n = 16384 and n = 65536 on seeded samples of initial regions
+  (each region is an independent subtree, so the reference renders it alone).
+"""
+import numpy as np
+import pytest
+
+from paper_2206_02255_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+NO_FILL = 2
+
+
+def params(asklib, g=16, r=2, B=32, block=(16, 16), count=False):
+    return asklib.make_params(g, r, B, block, asklib.FLAG_COUNT if count else 0)
+
+
+def gpu_map(ctx, method, window, n, M, p=None, stats=False):
+    import torch
+    res = ctx.render(method, window, n, M, p, stats=stats)
+    out, st = res if stats else (res, None)
+    torch.cuda.synchronize()
+    m = out.cpu().numpy().view(np.uint32).reshape(n, n)
+    return (m, st) if stats else m
+
+
+def first_diff(a, b):
+    idx = np.argwhere(a != b)
+    if len(idx) == 0:
+        return None
+    py, px = idx[0]
+    return "%d mismatches; first at (px=%d, py=%d): gpu %d vs oracle %d" % (
+        len(idx), px, py, a[py, px], b[py, px])
+
+
+# --------------------------------------------------------------------------
+# exhaustive
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("block", inputs.BLOCK_SHAPES)
+def test_exhaustive_c0(ctx, orc, asklib, block):
+    C = inputs.C0
+    want = orc.render_exhaustive(C["window"], C["n"], C["max_dwell"])
+    got = gpu_map(ctx, "exhaustive", C["window"], C["n"], C["max_dwell"],
+                  params(asklib, block=block))
+    assert first_diff(got, want) is None, first_diff(got, want)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 31, 33, 100, 257, 1000])
+def test_exhaustive_ragged(ctx, orc, asklib, n):
+    for win, M, block in [((-2.0, 0.5, -1.1, 1.3), 100, (8, 4)),
+                          ((-0.8, -0.6, 0.05, 0.30), 700, (32, 1)),
+                          ((-2.0, 0.47, -1.12, 1.12), 1, (16, 16)),
+                          ((-1.9, 0.6, -0.3, 1.2), 17, (64, 8))]:
+        want = orc.render_exhaustive(win, n, M)
+        got = gpu_map(ctx, "exhaustive", win, n, M, params(asklib, block=block))
+        assert first_diff(got, want) is None, (win, n, M, block, first_diff(got, want))
+
+
+def test_exhaustive_iteration_count(ctx, orc, asklib):
+    C = inputs.C0
+    want, it = orc.render_exhaustive(C["window"], C["n"], C["max_dwell"], return_iterations=True)
+    got, st = gpu_map(ctx, "exhaustive", C["window"], C["n"], C["max_dwell"],
+                      params(asklib, count=True), stats=True)
+    assert np.array_equal(got, want)
+    assert st["iterations"] == it == int(want.astype(np.uint64).sum())
+
+
+# --------------------------------------------------------------------------
+# ASK
+# --------------------------------------------------------------------------
+def _check_ms(ctx, orc, asklib, method, win, n, M, g, r, B, block=(16, 16), counts=True):
+    want, ost = orc.render_ms(win, n, M, g, r, B)
+    got, st = gpu_map(ctx, method, win, n, M, params(asklib, g, r, B, block), stats=True)
+    d = first_diff(got, want)
+    assert d is None, (method, win, n, M, g, r, B, block, d)
+    if counts:
+        assert st["levels"] >= ost["levels"]
+        L = ost["levels"]
+        if method == "ask":
+            assert st["regions_per_level"][:L] == ost["regions_per_level"]
+            assert all(v == 0 for v in st["regions_per_level"][L:])
+        assert st["fills_per_level"][:L] == ost["fills_per_level"]
+        assert st["subdivisions_per_level"][:L] == ost["subdivisions_per_level"]
+        assert st["leaves"] == ost["leaves"]
+    return got, st
+
+
+@pytest.mark.parametrize("block", inputs.BLOCK_SHAPES)
+def test_ask_c0(ctx, orc, asklib, block):
+    C = inputs.C0
+    _check_ms(ctx, orc, asklib, "ask", C["window"], C["n"], C["max_dwell"], C["g"], C["r"],
+              C["B"], block)
+
+
+def test_ask_c0_counters(ctx, orc, asklib):
+    """With counting on, pixels and iterations match what the reference's
+    region log implies (the leaf kernel skips perimeters already computed)."""
+    C = inputs.C0
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    ex = orc.render_exhaustive(win, n, M)
+    want, ost, log = orc.render_ms(win, n, M, C["g"], C["r"], C["B"], log=True)
+    got, st = gpu_map(ctx, "ask", win, n, M, params(asklib, C["g"], C["r"], C["B"], count=True),
+                      stats=True)
+    assert np.array_equal(got, want)
+    assert st["fill_pixels"] == ost["fill_pixels"]
+    assert st["border_pixels"] == ost["border_pixels"]
+    interior_px = interior_it = border_it = 0
+    for e in log:
+        x0, y0, w, h = (int(e[k]) for k in ("x0", "y0", "w", "h"))
+        blk = ex[y0:y0 + h, x0:x0 + w].astype(np.uint64)
+        per = blk.sum() - (blk[1:-1, 1:-1].sum() if w > 2 and h > 2 else 0)
+        border_it += int(per)
+        if e["kind"] == 2 and w > 2 and h > 2:
+            interior_px += (w - 2) * (h - 2)
+            interior_it += int(blk[1:-1, 1:-1].sum())
+    assert st["leaf_pixels"] == interior_px
+    assert st["iterations"] == border_it + interior_it
+
+
+@pytest.mark.parametrize("g,r,B", inputs.c1_sweep())
+def test_ask_sweep_n2048(ctx, orc, asklib, g, r, B):
+    """The (g, r, B) sweep of the n = 16384 configuration at n = 2048."""
+    _check_ms(ctx, orc, asklib, "ask", inputs.WINDOW_PAPER, 2048, 2048, g, r, B)
+
+
+def test_ask_tiny_all_parameters(ctx, orc, asklib):
+    """Every (g, r, B) in {1, 2, 3, 4, 8}^3 (r >= 2, g <= n) on tiny grids."""
+    wins = [(-2.0, 0.6, -1.25, 1.25), (-0.8, -0.6, 0.05, 0.30)]
+    for n in (1, 2, 3, 5, 8, 16):
+        for win in wins:
+            want_nf = orc.render_exhaustive(win, n, 60)
+            for g in (1, 2, 3, 4, 8):
+                if g > n:
+                    continue
+                for r in (2, 3, 4, 8):
+                    for B in (1, 2, 3, 4, 8):
+                        want, _ = orc.render_ms(win, n, 60, g, r, B, threads=1)
+                        got = gpu_map(ctx, "ask", win, n, 60, params(asklib, g, r, B, (8, 4)))
+                        d = first_diff(got, want)
+                        assert d is None, (n, win, g, r, B, d)
+            assert want_nf.shape == (n, n)
+
+
+@pytest.mark.parametrize("n,g,r,B", [(100, 3, 2, 4), (257, 5, 3, 2), (1000, 7, 2, 8),
+                                     (1023, 16, 2, 16), (4099, 13, 4, 16), (3001, 32, 8, 1),
+                                     (777, 777, 2, 1), (500, 2, 64, 1)])
+def test_ask_ragged(ctx, orc, asklib, n, g, r, B):
+    for win, M in [(inputs.WINDOW_PAPER, 300), (inputs.WINDOW_WIDE, 97)]:
+        _check_ms(ctx, orc, asklib, "ask", win, n, M, g, r, B, (32, 8))
+
+
+def test_ask_random_windows(ctx, orc, asklib):
+    for k, win in enumerate(inputs.random_windows(12, seed=3)):
+        n = [64, 200, 512, 999][k % 4]
+        _check_ms(ctx, orc, asklib, "ask", win, n, 400, [2, 4, 8][k % 3], [2, 4][k % 2],
+                  [4, 8, 16][k % 3], (16, 16))
+
+
+def test_ask_repeat_and_async(ctx, orc, asklib):
+    """Two renders on a side stream without synchronisation in between, then
+    one with stats: identical maps."""
+    import torch
+    C = inputs.C0
+    p = params(asklib, C["g"], C["r"], C["B"])
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            outs.append(ctx.render("ask", C["window"], C["n"], C["max_dwell"], p))
+    s.synchronize()
+    ctx.check(s)
+    want, _ = orc.render_ms(C["window"], C["n"], C["max_dwell"], C["g"], C["r"], C["B"])
+    for o in outs:
+        assert np.array_equal(o.cpu().numpy().view(np.uint32), want)
+
+
+def test_render_host(ctx, orc, asklib):
+    C = inputs.C0
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    want, _ = orc.render_ms(win, n, M, C["g"], C["r"], C["B"])
+    got = ctx.render_host("ask", win, n, M, params(asklib, C["g"], C["r"], C["B"]))
+    assert np.array_equal(got, want)
+    got = ctx.render_host("exhaustive", win, n, M, params(asklib))
+    assert np.array_equal(got, orc.render_exhaustive(win, n, M))
+
+
+# --------------------------------------------------------------------------
+# CDP2
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("g,r,B,block", [(16, 2, 32, (16, 16)), (32, 4, 16, (64, 8)),
+                                         (8, 2, 16, (8, 8)), (4, 8, 4, (32, 32))])
+def test_cdp2_c0(ctx, orc, asklib, g, r, B, block):
+    C = inputs.C0
+    _check_ms(ctx, orc, asklib, "cdp2", C["window"], C["n"], C["max_dwell"], g, r, B, block)
+
+
+@pytest.mark.parametrize("n,g,r,B", [(5, 2, 2, 1), (37, 3, 2, 4), (257, 5, 3, 2),
+                                     (1000, 7, 2, 8), (2048, 32, 4, 16)])
+def test_cdp2_ragged(ctx, orc, asklib, n, g, r, B):
+    _check_ms(ctx, orc, asklib, "cdp2", inputs.WINDOW_WIDE, n, 200, g, r, B, (16, 16))
+
+
+# --------------------------------------------------------------------------
+# argument errors
+# --------------------------------------------------------------------------
+def _raw_render(ctx, asklib, method, win, n, M, p, ptr):
+    import ctypes
+    from paper_2206_02255_gb300.ask import Window, lib
+    return lib().ask_render(ctx.handle, method, ctypes.byref(Window(*win)), n, M,
+                            ctypes.byref(p) if p is not None else None, ctypes.c_void_p(ptr),
+                            None, None)
+
+
+def test_invalid_arguments(ctx, asklib):
+    """Bad arguments return EINVAL before anything is launched: the output
+    keeps its old contents."""
+    import torch
+    W = inputs.WINDOW_PAPER
+    out = torch.full((64, 64), 7, dtype=torch.int32, device="cuda")
+    ptr = out.data_ptr()
+    A, E, C = asklib.METHOD_ASK, asklib.METHOD_EXHAUSTIVE, asklib.METHOD_CDP2
+    bad = [
+        (A, W, 64, 100, params(asklib, g=0), ptr),
+        (A, W, 64, 100, params(asklib, g=65), ptr),
+        (A, W, 64, 100, params(asklib, r=1), ptr),
+        (A, W, 64, 100, params(asklib, r=65), ptr),
+        (A, W, 64, 100, params(asklib, B=0), ptr),
+        (A, W, 64, 0, params(asklib), ptr),
+        (A, W, 64, 0xffffffff, params(asklib), ptr),
+        (A, (0.5, -1.5, -1.0, 1.0), 64, 100, params(asklib), ptr),
+        (A, (-1.0, -1.0, -1.0, 1.0), 64, 100, params(asklib), ptr),
+        (A, (float("nan"), 0.5, -1.0, 1.0), 64, 100, params(asklib), ptr),
+        (A, (float("-inf"), 0.5, -1.0, 1.0), 64, 100, params(asklib), ptr),
+        (A, W, 64, 100, params(asklib, block=(5, 5)), ptr),
+        (A, W, 64, 100, params(asklib, block=(2048, 1)), ptr),
+        (E, W, 64, 100, params(asklib, block=(4, 4)), ptr),
+        (A, W, 64, 100, None, ptr),
+        (C, W, 64, 100, None, ptr),
+        (7, W, 64, 100, params(asklib), ptr),
+        (A, W, 0, 100, params(asklib), ptr),
+        (A, W, 65537, 100, params(asklib, g=2), ptr),
+        (A, W, 64, 100, params(asklib), 0),
+        (A, W, 8, 100, params(asklib, g=2, B=2), ptr + 4),      # not 16-byte aligned
+        (E, W, 8, 100, params(asklib), ptr + 8),
+    ]
+    flags_bad = params(asklib)
+    flags_bad.flags = 0x80
+    bad.append((A, W, 64, 100, flags_bad, ptr))
+    for method, win, n, M, p, q in bad:
+        st = _raw_render(ctx, asklib, method, win, n, M, p, q)
+        assert st == asklib.EINVAL, (method, win, n, M, st)
+    torch.cuda.synchronize()
+    assert bool((out == 7).all())
+    with pytest.raises(asklib.AskError) as e:
+        ctx.render("ask", W, 64, 100, params(asklib, g=0), out=out)
+    assert e.value.status == asklib.EINVAL and "g must be" in str(e.value)
+
+
+# --------------------------------------------------------------------------
+# full size, sampled
+# --------------------------------------------------------------------------
+def _sampled_regions(ctx, orc, asklib, method, win, n, M, g, r, B, block, k, seed, full=None):
+    if full is None:
+        full = gpu_map(ctx, method, win, n, M, params(asklib, g, r, B, block))
+    for gx, gy in inputs.sample_initial_regions(g, k, seed):
+        res = orc.render_ms_region(win, n, M, g, r, B, gx, gy)
+        if res is None:
+            continue
+        (x0, y0, w, h), tile, _ = res
+        d = first_diff(full[y0:y0 + h, x0:x0 + w], tile)
+        assert d is None, (method, n, g, r, B, gx, gy, d)
+    return full
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("g,r,B", [(32, 4, 16), (16, 2, 32), (32, 2, 16), (8, 8, 64)])
+def test_c1_ask_sampled(ctx, orc, asklib, g, r, B):
+    C = inputs.C1
+    _sampled_regions(ctx, orc, asklib, "ask", C["window"], C["n"], C["max_dwell"], g, r, B,
+                     (16, 16), k=6, seed=g * 1000 + r * 10 + B)
+
+
+@pytest.mark.slow
+def test_c1_cdp2_equals_ask(ctx, orc, asklib):
+    C = inputs.C1
+    p = (C["window"], C["n"], C["max_dwell"])
+    a = gpu_map(ctx, "ask", *p, params(asklib, 32, 4, 16))
+    c = gpu_map(ctx, "cdp2", *p, params(asklib, 32, 4, 16))
+    assert first_diff(c, a) is None
+    _sampled_regions(ctx, orc, asklib, "cdp2", *p, 32, 4, 16, (16, 16), k=3, seed=5, full=c)
+
+
+@pytest.mark.slow
+def test_c1_exhaustive_sampled(ctx, orc, asklib):
+    C = inputs.C1
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    full = gpu_map(ctx, "exhaustive", win, n, M, params(asklib))
+    for px, py in inputs.sample_pixels(n, 3000, seed=11):
+        cr, ci = orc.pixel_to_c(win, n, px, py)
+        assert full[py, px] == orc.dwell(cr, ci, M), (px, py)
+    # one initial-region-sized block, the reference with fills disabled
+    (x0, y0, w, h), tile, _ = orc.render_ms_region(win, n, M, 32, 2, 1 << 20, 20, 14, flags=NO_FILL)
+    assert np.array_equal(full[y0:y0 + h, x0:x0 + w], tile)
+
+
+@pytest.mark.slow
+def test_c2_ask_and_exhaustive_sampled(ctx, orc, asklib):
+    """n = 65536 (17.2 GB map): ASK at g = 32, r = 4, B = 16 on sampled initial
+    regions, the exhaustive kernel on sampled pixels."""
+    import torch
+    C = inputs.C2
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    out = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    ctx.render("ask", win, n, M, params(asklib, 32, 4, 16), out=out)
+    torch.cuda.synchronize()
+    ctx.check()
+    for gx, gy in inputs.sample_initial_regions(32, 3, seed=65536):
+        (x0, y0, w, h), tile, _ = orc.render_ms_region(win, n, M, 32, 4, 16, gx, gy)
+        got = out[y0:y0 + h, x0:x0 + w].cpu().numpy().view(np.uint32)
+        assert first_diff(got, tile) is None, (gx, gy, first_diff(got, tile))
+    ctx.render("exhaustive", win, n, M, params(asklib), out=out)
+    torch.cuda.synchronize()
+    pts = inputs.sample_pixels(n, 2000, seed=12)
+    idx = torch.tensor([py * n + px for px, py in pts], dtype=torch.int64, device="cuda")
+    vals = out.view(-1)[idx].cpu().numpy().view(np.uint32)
+    for (px, py), v in zip(pts, vals):
+        cr, ci = orc.pixel_to_c(win, n, px, py)
+        assert v == orc.dwell(cr, ci, M), (px, py)
+    del out
+    torch.cuda.empty_cache()
