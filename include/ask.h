@@ -65,7 +65,8 @@ typedef enum {
     ASK_ECUDA = 3,         /* a CUDA runtime call failed; see ask_last_error */
     ASK_EOVERFLOW = 4,     /* a device-side capacity check failed */
     ASK_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
-    ASK_EUNSUPPORTED = 6   /* the device is not sm_103 or lacks a feature */
+    ASK_EUNSUPPORTED = 6,  /* the device is not sm_103 or lacks a feature */
+    ASK_ECAPACITY = 7      /* ask_render_noalloc: request exceeds its fixed scratch */
 } ask_status;
 
 typedef enum {
@@ -172,6 +173,25 @@ ask_status ask_check(ask_ctx *ctx, void *stream);
 ask_status ask_plan_levels(uint32_t n, uint32_t g, uint32_t r, uint32_t B,
                            uint32_t *sides, uint64_t *max_regions, uint32_t cap,
                            uint32_t *levels);
+
+/* ASK render that allocates nothing (the paper has no counterpart: this is a
+ * service for callers).  For callers that may not call cudaMalloc -- a frame
+ * loop or host callback where an allocation and the synchronisation it may
+ * cause are not allowed, a plug-in whose host application owns all device
+ * memory, a service held to a fixed memory budget.  The scratch comes from
+ * arrays with static storage on the device, shared by every call: at most
+ * 2^20 regions per subdivision level and 2^20 leaves (about 24 MiB on every
+ * device that loads the library, held until the process exits), e.g. n up
+ * to 16384 with B >= 16, or n up to 4096 with B >= 4.  A larger plan returns
+ * ASK_ECAPACITY before anything is launched; other argument errors return
+ * ASK_EINVAL.  params->flags must be 0.  The call is asynchronous on `stream`
+ * and renders into the caller's d_dwell (n*n uint32, 16-byte aligned) on the
+ * current device.  The first call on a device looks up the scratch addresses
+ * (cudaGetSymbolAddress); make it before any stream capture.  Calls whose
+ * work overlaps on the GPU share the scratch and race: order them on one
+ * stream.  Each call clears the counters it needs on its stream first. */
+ask_status ask_render_noalloc(const ask_window *window, uint32_t n, uint32_t max_dwell,
+                              const ask_params *params, uint32_t *d_dwell, void *stream);
 
 /* Human-readable name of a status code (static storage). */
 const char *ask_status_str(ask_status status);

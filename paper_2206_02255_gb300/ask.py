@@ -17,7 +17,7 @@ from . import build as _build
 
 ASK_MAX_LEVELS = 32
 
-OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EUNSUPPORTED = range(7)
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EUNSUPPORTED, ECAPACITY = range(8)
 METHOD_EXHAUSTIVE, METHOD_ASK, METHOD_CDP2 = 0, 1, 2
 FLAG_COUNT = 1
 FLAG_TIMING = 2
@@ -104,6 +104,8 @@ SIGNATURES = {
     "ask_plan_levels": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_uint32, _P(ctypes.c_uint32), _P(ctypes.c_uint64),
                                        ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "ask_render_noalloc": (ctypes.c_int, [_P(Window), ctypes.c_uint32, ctypes.c_uint32,
+                                          _P(Params), ctypes.c_void_p, ctypes.c_void_p]),
     "ask_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "ask_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ask_version": (ctypes.c_char_p, []),
@@ -149,6 +151,27 @@ def plan_levels(n, g, r, B):
         raise AskError(st, "ask_plan_levels(%d, %d, %d, %d): %s" % (n, g, r, B, status_str(st)))
     L = levels.value
     return list(sides[:L]), list(regs[:L])
+
+
+def render_noalloc(window, n, max_dwell, params, out, stream=None):
+    """ASK render that allocates nothing on the device (``ask_render_noalloc``):
+    for callers that may not call cudaMalloc.  ``out`` is a caller-owned
+    contiguous CUDA tensor of n*n 4-byte elements; the scratch is the
+    library's fixed device arrays (at most 2^20 regions per level), shared
+    by every call, so calls must not overlap on the GPU.  Asynchronous on
+    ``stream`` (default: torch's current stream on ``out``'s device)."""
+    import torch
+    if not out.is_cuda or out.numel() != n * n or out.element_size() != 4 or \
+            not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor of n*n 4-byte elements")
+    s = stream if stream is not None else torch.cuda.current_stream(out.device)
+    with torch.cuda.device(out.device):
+        st = lib().ask_render_noalloc(ctypes.byref(_window(window)), n, max_dwell,
+                                      ctypes.byref(params), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(s.cuda_stream))
+    if st != OK:
+        raise AskError(st, "ask_render_noalloc: %s" % status_str(st))
+    return out
 
 
 def make_params(g=16, r=2, B=32, block=(16, 16), flags=0):

@@ -532,6 +532,7 @@ const char *ask_status_str(ask_status s)
     case ASK_EOVERFLOW: return "device capacity overflow";
     case ASK_ETIMEOUT: return "device wait timed out";
     case ASK_EUNSUPPORTED: return "unsupported device";
+    case ASK_ECAPACITY: return "request exceeds the fixed scratch of ask_render_noalloc";
     }
     return "unknown status";
 }
