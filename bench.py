@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--block", default="16x16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="override n (small cases for profiling; not the headline)")
+    ap.add_argument("--max-dwell", type=int, default=None)
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the exhaustive and CDP2 comparison arms")
     return ap.parse_args()
 
 
@@ -203,7 +208,11 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    C = inputs.C1
+    C = dict(inputs.C1)
+    if args.n or args.max_dwell:
+        C["n"] = args.n or C["n"]
+        C["max_dwell"] = args.max_dwell or C["max_dwell"]
+        C["name"] = "mandelbrot_n%d_d%d" % (C["n"], C["max_dwell"])
     win, n, M = C["window"], C["n"], C["max_dwell"]
     ctx = ask.Context(local)
     out = torch.empty((n, n), dtype=torch.int32, device=dev)
@@ -274,8 +283,12 @@ def run_gpu(args):
     timing = ctx.timing_read()
 
     # ---- comparison arms at the same configuration (untimed for the headline)
-    ms_ex = time_renders("exhaustive", g, r, B, blk, max(3, args.steps // 4))
-    ms_cdp = time_renders("cdp2", g, r, B, blk, max(3, args.steps // 4))
+    ms_ex = ms_cdp = ms_cdp_fnf = float("nan")
+    if not args.no_compare:
+        reps = max(3, args.steps // 4)
+        ms_ex = time_renders("exhaustive", g, r, B, blk, reps)
+        ms_cdp = time_renders("cdp2", g, r, B, blk, 2)
+        ms_cdp_fnf = time_renders("cdp2", g, r, B, blk, reps, ask.FLAG_CDP2_FIRE_AND_FORGET)
 
     pixels = float(n) * n
     value = world * pixels / (ms_step / 1e3) / 1e9
@@ -340,11 +353,16 @@ def run_gpu(args):
                              "exhaustive_equivalent": est["iterations"] / (ms_step / 1e3)},
             "exhaustive": {"ms": ms_ex, "gpix_s": pixels / (ms_ex / 1e3) / 1e9,
                            "dwell_iter_s": est["iterations"] / (ms_ex / 1e3)},
-            "cdp2": {"ms": ms_cdp, "gpix_s": pixels / (ms_cdp / 1e3) / 1e9},
-            "speedup_vs_exhaustive": ms_ex / ms_step, "speedup_vs_cdp2": ms_cdp / ms_step,
+            "cdp2": {"ms_tail_launch": ms_cdp, "ms_fire_and_forget": ms_cdp_fnf,
+                     "gpix_s": pixels / (min(ms_cdp, ms_cdp_fnf) / 1e3) / 1e9},
+            "speedup_vs_exhaustive": ms_ex / ms_step,
+            "speedup_vs_cdp2": min(ms_cdp, ms_cdp_fnf) / ms_step,
             "mismatch_vs_exhaustive_pixels": mismatch,
             "kernels_ms": kern, "levels": cst["levels"],
             "regions_per_level": cst["regions_per_level"], "leaves": cst["leaves"],
+            "fills_per_level": cst["fills_per_level"],
+            "iterations_per_level": cst["iterations_per_level"],
+            "leaf_iterations": cst["leaf_iterations"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,

@@ -78,6 +78,9 @@ typedef enum {
 /* flags of ask_params */
 #define ASK_FLAG_COUNT 1u   /* count dwell iterations and pixels per kind (slower) */
 #define ASK_FLAG_TIMING 2u  /* record per-kernel device times (read with ask_timing_read) */
+#define ASK_FLAG_CDP2_FIRE_AND_FORGET 4u /* CDP2: launch children into the fire-and-forget
+                                          * stream (concurrent) instead of the tail-launch
+                                          * stream (children of one grid run in order) */
 
 typedef struct {
     float re_min, re_max, im_min, im_max;

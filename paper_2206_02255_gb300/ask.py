@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EUNSUPPORTED, ECAPACITY = range(
 METHOD_EXHAUSTIVE, METHOD_ASK, METHOD_CDP2 = 0, 1, 2
 FLAG_COUNT = 1
 FLAG_TIMING = 2
+FLAG_CDP2_FIRE_AND_FORGET = 4
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 

@@ -160,7 +160,7 @@ ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window,
         return set_err(ctx, ASK_EINVAL, "params are required for subdivision methods");
     if (!block_ok(d.block_x, d.block_y))
         return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
-    if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING))
+    if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET))
         return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
     if (method != ASK_METHOD_EXHAUSTIVE) {
         if (d.g == 0 || d.g > n)
@@ -412,6 +412,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.r = p.r;
         a.B = p.B;
         a.count = count ? 1u : 0u;
+        a.fire_and_forget = (p.flags & ASK_FLAG_CDP2_FIRE_AND_FORGET) ? 1u : 0u;
         a.ctr = ctx->ctr;
         if ((e = launch_cdp2(a, p.g, plan.side[0], p.block_x, p.block_y, s)) != cudaSuccess)
             return cuda_err(ctx, e, "CDP2 root kernel");

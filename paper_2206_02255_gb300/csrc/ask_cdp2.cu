@@ -2,9 +2,12 @@
 // Parallelism (paper Sec. 3; the DP implementations compared in Sec. 6),
 // written for the CDP2 device runtime of CUDA 12+: a subdividing region
 // launches one child grid, r x r CTAs (one per non-empty sub-region, the SBR
-// mapping of Sec. 4.3.1), into the tail-launch stream, so no parent ever
-// waits on a child.  The host sees the render complete when the whole tree
-// of grids has completed.
+// mapping of Sec. 4.3.1), so no parent ever waits on a child.  By default the
+// child goes into the tail-launch stream: it starts once the parent grid has
+// finished, and the tail launches of one grid run in launch order.  With
+// ASK_FLAG_CDP2_FIRE_AND_FORGET it goes into the fire-and-forget stream and
+// runs concurrently with its parent and siblings.  The host sees the render
+// complete when the whole tree of grids has completed.
 //
 // This translation unit is compiled with relocatable device code and linked
 // against the device runtime; the rest of the library is not.
@@ -38,7 +41,7 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
 {
     extern __shared__ uint32_t stage[];
     __shared__ uint32_t red_min[32], red_max[32];
-    __shared__ uint32_t s_min, s_max;
+    __shared__ uint32_t s_min, s_max, s_flag, s_w;
 
     const uint32_t x0 = px0 + blockIdx.x * side, y0 = py0 + blockIdx.y * side;
     if (x0 >= px0 + pw || y0 >= py0 + ph)
@@ -53,60 +56,82 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
     const uint32_t tid = threadIdx.x + threadIdx.y * blockDim.x;
     const uint32_t lane = tid & 31u, wid = tid >> 5, nw = T >> 5;
     const uint32_t stage_cap = min(4u * side, kStageMax);
+    const uint32_t sc = ceil_div_u32(side, a.r);
+    const bool split = side > 1u && sc >= a.B;
     unsigned long long it = 0;
-
-    // exploration query: perimeter dwells, staged in shared memory
     const uint32_t P = perimeter_size(g.w, g.h);
-    uint32_t dmin = 0xffffffffu, dmax = 0u;
-    for (uint32_t k = tid; k < P; k += T) {
-        uint32_t px, py;
-        perimeter_pixel(g, k, px, py);
-        const float2 c = pixel_c(a.pm, px, py);
-        const uint32_t d = dwell(c.x, c.y, a.max_dwell);
-        dmin = min(dmin, d);
-        dmax = max(dmax, d);
-        if (k < stage_cap)
-            stage[k] = d;
-        else
-            a.map[(size_t)py * a.n + px] = d;
-        it += d;
-    }
-    dmin = __reduce_min_sync(kFull, dmin);
-    dmax = __reduce_max_sync(kFull, dmax);
-    if (lane == 0) {
-        red_min[wid] = dmin;
-        red_max[wid] = dmax;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
-        uint32_t m1 = lane < nw ? red_max[lane] : 0u;
-        m0 = __reduce_min_sync(kFull, m0);
-        m1 = __reduce_max_sync(kFull, m1);
-        if (lane == 0) {
-            s_min = m0;
-            s_max = m1;
+    uint32_t dmin, dmax;
+
+    if (split) {
+        // exploration query that stops at the first difference
+        if (tid == 0) {
+            s_flag = 0u;
+            s_w = 0xffffffffu;
         }
+        __syncthreads();
+        uint32_t wv = 0;
+        const bool uni = cta_perimeter_uniform(a.pm, a.max_dwell, g, tid, T, &s_flag, &s_w, &wv, it);
+        dmin = wv;
+        dmax = uni ? wv : wv + 1u;
+    } else {
+        // exploration query of a region that would be a leaf: perimeter
+        // dwells staged in shared memory
+        dmin = 0xffffffffu;
+        dmax = 0u;
+        for (uint32_t k = tid; k < P; k += T) {
+            uint32_t px, py;
+            perimeter_pixel(g, k, px, py);
+            const float2 c = pixel_c(a.pm, px, py);
+            const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+            dmin = min(dmin, d);
+            dmax = max(dmax, d);
+            if (k < stage_cap)
+                stage[k] = d;
+            else
+                a.map[(size_t)py * a.n + px] = d;
+            it += d;
+        }
+        dmin = __reduce_min_sync(kFull, dmin);
+        dmax = __reduce_max_sync(kFull, dmax);
+        if (lane == 0) {
+            red_min[wid] = dmin;
+            red_max[wid] = dmax;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
+            uint32_t m1 = lane < nw ? red_max[lane] : 0u;
+            m0 = __reduce_min_sync(kFull, m0);
+            m1 = __reduce_max_sync(kFull, m1);
+            if (lane == 0) {
+                s_min = m0;
+                s_max = m1;
+            }
+        }
+        __syncthreads();
+        dmin = s_min;
+        dmax = s_max;
     }
-    __syncthreads();
-    dmin = s_min;
-    dmax = s_max;
 
     if (dmin == dmax) {
         fill_rect(a.map, a.n, g, dmin, tid, T);
         if (tid == 0)
             atomicAdd(&a.ctr->fills[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
     } else {
-        const uint32_t sc = ceil_div_u32(side, a.r);
-        if (side > 1u && sc >= a.B) {
+        if (split) {
             if (tid == 0) {
                 atomicAdd(&a.ctr->subdivs[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
                 const uint32_t cx = min(a.r, ceil_div_u32(g.w, sc));
                 const uint32_t cy = min(a.r, ceil_div_u32(g.h, sc));
                 const size_t smem = (size_t)min(4u * sc, kStageMax) * sizeof(uint32_t);
-                cdp2_region_kernel<<<dim3(cx, cy), dim3(blockDim.x, blockDim.y), smem,
-                                     cudaStreamTailLaunch>>>(a, g.x0, g.y0, g.w, g.h, sc,
-                                                             level + 1u);
+                if (a.fire_and_forget)
+                    cdp2_region_kernel<<<dim3(cx, cy), dim3(blockDim.x, blockDim.y), smem,
+                                         cudaStreamFireAndForget>>>(a, g.x0, g.y0, g.w, g.h, sc,
+                                                                    level + 1u);
+                else
+                    cdp2_region_kernel<<<dim3(cx, cy), dim3(blockDim.x, blockDim.y), smem,
+                                         cudaStreamTailLaunch>>>(a, g.x0, g.y0, g.w, g.h, sc,
+                                                                 level + 1u);
                 if (cudaGetLastError() != cudaSuccess)
                     atomicOr(&a.ctr->error, ERR_DEVICE_LAUNCH);
             }

@@ -10,8 +10,11 @@
 
 namespace ask {
 
-// Iterations per escape check block in dwell(); see the comment there.
+// Updates per unchecked block in the dwell loops (see dwell()).
 constexpr int kUnroll = 16;
+
+// |c|^2 bound below which escape is absorbing in float arithmetic (see dwell()).
+constexpr float kAbsorbR2 = 3.999f;
 
 __device__ __forceinline__ float2 pixel_c(const PixelMap &pm, uint32_t px, uint32_t py)
 {
@@ -19,55 +22,127 @@ __device__ __forceinline__ float2 pixel_c(const PixelMap &pm, uint32_t px, uint3
                        __fmaf_rn(__uint2float_rn(py), pm.dy, pm.im_min));
 }
 
+// One update z <- z^2 + c, each operation rounded once (the _rn intrinsics
+// are never fused or reassociated by the compiler):
+//   zr' = fma(zr, zr, fma(-zi, zi, cr)),  zi' = fma(zr + zr, zi, ci).
+__device__ __forceinline__ void z_update(float &x, float &y, float cr, float ci)
+{
+    const float t = __fmaf_rn(-y, y, cr);
+    const float nx = __fmaf_rn(x, x, t);
+    const float ny = __fmaf_rn(__fadd_rn(x, x), y, ci);
+    x = nx;
+    y = ny;
+}
+
+// The escape test of the current state: |z|^2 = fma(zr, zr, zi*zi) < 4.
+__device__ __forceinline__ bool z_bounded(float x, float y)
+{
+    return __fmaf_rn(x, x, __fmul_rn(y, y)) < 4.0f;
+}
+
+// Escape is absorbing when |c| < 2 - 2.4e-4, i.e. fma(cr, cr, ci*ci) < 3.999:
+// if the rounded |z_j|^2 >= 4 then the exact |z_j|^2 > 4 - 4e-7, so the exact
+// |z_j^2 + c| > 2 + 2.3e-4, and the rounding of one update (a few ulps of
+// |z|^2) cannot take it back below 2; by induction |z| keeps growing until it
+// overflows, and an inf or NaN state also fails the test "|z|^2 < 4".  So for
+// such c, a state that passes the test proves that every earlier state passed.
+__device__ __forceinline__ bool escape_absorbing(float cr, float ci)
+{
+    return __fmaf_rn(cr, cr, __fmul_rn(ci, ci)) < kAbsorbR2;
+}
+
 // Dwell of c (paper Sec. 6): the number of updates z <- z^2 + c, from z = 0,
-// made while |z|^2 < 4, at most max_dwell.  One iteration is
-//   zi2 = zi*zi; m = fma(zr, zr, zi2)          (the escape test on m)
-//   zr' = fma(zr, zr, fma(-zi, zi, cr)); zi' = fma(zr + zr, zi, ci)
-// with every operation rounded once (the _rn intrinsics are never fused or
-// reassociated by the compiler).
+// made while |z|^2 < 4, at most max_dwell.
 //
-// To keep the FP32 pipe busy, iterations run in blocks of kUnroll with the
-// escape tests OR-ed into one predicate and a single branch per block; a
-// block whose predicate fired is rolled back to its saved start and replayed
-// one checked step at a time, so the result is exactly the stepwise count.
+// Where escape is absorbing, updates run in blocks of kUnroll with a single
+// test on the block's last state: 3 FFMA + 1 FADD per update, the test
+// amortised over the block.  A block whose last state fails the test is
+// rolled back and replayed one tested update at a time, so the count is
+// exactly the stepwise one.  Other points, and the tail below max_dwell, take
+// the tested loop.
 __device__ __forceinline__ uint32_t dwell(float cr, float ci, uint32_t max_dwell)
 {
     float x = 0.0f, y = 0.0f;
     uint32_t d = 0;
-    while (max_dwell - d >= (uint32_t)kUnroll) {
-        const float sx = x, sy = y;
-        bool out = false;
+    if (escape_absorbing(cr, ci)) {
+        while (max_dwell - d >= (uint32_t)kUnroll) {
+            const float sx = x, sy = y;
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) {
-            const float y2 = __fmul_rn(y, y);
-            const float m = __fmaf_rn(x, x, y2);
-            out |= !(m < 4.0f);
-            const float t = __fmaf_rn(-y, y, cr);
-            const float nx = __fmaf_rn(x, x, t);
-            const float ny = __fmaf_rn(__fadd_rn(x, x), y, ci);
-            x = nx;
-            y = ny;
+            for (int k = 0; k < kUnroll; ++k)
+                z_update(x, y, cr, ci);
+            if (!z_bounded(x, y)) {
+                x = sx;
+                y = sy;
+                break;
+            }
+            d += (uint32_t)kUnroll;
         }
-        if (out) {
-            x = sx;
-            y = sy;
-            break;
-        }
-        d += (uint32_t)kUnroll;
     }
-    while (d < max_dwell) {
-        const float y2 = __fmul_rn(y, y);
-        const float m = __fmaf_rn(x, x, y2);
-        if (!(m < 4.0f))
-            break;
-        const float t = __fmaf_rn(-y, y, cr);
-        const float nx = __fmaf_rn(x, x, t);
-        const float ny = __fmaf_rn(__fadd_rn(x, x), y, ci);
-        x = nx;
-        y = ny;
+    while (d < max_dwell && z_bounded(x, y)) {
+        z_update(x, y, cr, ci);
         ++d;
     }
     return d;
+}
+
+// Resumable orbit of one point, for perimeter queries that stop early.
+struct Orbit {
+    float x, y, cr, ci;
+    uint32_t d;     // updates made; every state before z_d passed the test
+    bool fast;      // escape is absorbing for this c
+};
+
+__device__ __forceinline__ Orbit orbit_start(float2 c)
+{
+    Orbit o;
+    o.x = 0.0f;
+    o.y = 0.0f;
+    o.cr = c.x;
+    o.ci = c.y;
+    o.d = 0;
+    o.fast = escape_absorbing(c.x, c.y);
+    return o;
+}
+
+// Advance an orbit by up to kUnroll updates without passing `limit`.
+// Returns true when it is finished: it escaped (o.d is its dwell) or it made
+// `limit` updates (o.d = limit: the dwell is at least limit).  A round never
+// finishes an orbit at o.d equal to the round's last count unless the state
+// there was tested, so orbits that are still running after a round have a
+// dwell strictly above the dwell of any orbit that finished in it.
+__device__ __forceinline__ bool orbit_round(Orbit &o, uint32_t limit)
+{
+    if (o.d >= limit)
+        return true;
+    if (o.fast && limit - o.d >= (uint32_t)kUnroll) {
+        float x = o.x, y = o.y;
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k)
+            z_update(x, y, o.cr, o.ci);
+        if (z_bounded(x, y)) {
+            o.x = x;
+            o.y = y;
+            o.d += (uint32_t)kUnroll;
+            return o.d >= limit;
+        }
+        // some state of this block escaped: replay the block with tests
+        for (int k = 0; k < kUnroll; ++k) {
+            if (!z_bounded(o.x, o.y))
+                return true;
+            z_update(o.x, o.y, o.cr, o.ci);
+            ++o.d;
+        }
+        return false;  // the block's last state escapes; the next round sees it
+    }
+    for (int k = 0; k < kUnroll; ++k) {
+        if (o.d >= limit)
+            return true;
+        if (!z_bounded(o.x, o.y))
+            return true;
+        z_update(o.x, o.y, o.cr, o.ci);
+        ++o.d;
+    }
+    return o.d >= limit;
 }
 
 // Region record of the offset lookup tables (Sec. 5.2): origin and clipped
@@ -151,6 +226,137 @@ __device__ __forceinline__ void fill_rect(uint32_t *__restrict__ map, uint32_t n
                     map[e0 + k] = v;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Perimeter uniformity queries for regions that split when not uniform.
+//
+// Such a region needs only the answer "all perimeter dwells equal, and to
+// what", not the dwells themselves (its children evaluate their own
+// perimeters).  The orbits of a group of 32 perimeter pixels advance in
+// rounds; running orbits stay in lockstep, so as soon as one orbit has
+// finished while another still runs, their dwells differ and the query
+// stops.  Once one group has finished with a common dwell w, later groups
+// stop at w + 1 updates: more updates than w already means a different dwell.
+// ---------------------------------------------------------------------------
+constexpr unsigned kLaneMask = 0xffffffffu;
+
+// One warp queries the whole perimeter of g.  Returns true and the common
+// dwell in *w_out if the perimeter is uniform; `it` gains the updates made.
+__device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint32_t max_dwell,
+                                                       const Region &g, uint32_t lane,
+                                                       uint32_t *w_out, unsigned long long &it)
+{
+    const uint32_t P = perimeter_size(g.w, g.h);
+    bool have = false;
+    uint32_t w = 0;
+    for (uint32_t base = 0; base < P; base += 32u) {
+        const uint32_t k = base + lane;
+        const bool active = k < P;
+        const unsigned amask = __ballot_sync(kLaneMask, active);
+        uint32_t px = g.x0, py = g.y0;
+        if (active)
+            perimeter_pixel(g, k, px, py);
+        Orbit o = orbit_start(pixel_c(pm, px, py));
+        bool done = !active;
+        const uint32_t limit = have ? min(max_dwell, w + 1u) : max_dwell;
+        bool differ = false;
+        for (;;) {
+            if (!done)
+                done = orbit_round(o, limit);
+            const unsigned dm = __ballot_sync(kLaneMask, done) & amask;
+            if (dm == amask)
+                break;
+            if (dm) {
+                differ = true;
+                break;
+            }
+        }
+        if (active)
+            it += o.d;
+        if (differ)
+            return false;
+        const uint32_t vmin = __reduce_min_sync(kLaneMask, active ? o.d : 0xffffffffu);
+        const uint32_t vmax = __reduce_max_sync(kLaneMask, active ? o.d : 0u);
+        if (vmin != vmax || (have && vmin != w))
+            return false;
+        have = true;
+        w = vmin;
+    }
+    *w_out = w;
+    return true;
+}
+
+// All warps of a CTA query the perimeter of g together; warps share the
+// verdict through s_flag (1 = not uniform) and the common dwell through s_w
+// (0xffffffff = none yet).  The caller sets *s_flag = 0 and *s_w = 0xffffffff
+// and synchronises the CTA before the call; the call ends with a CTA barrier.
+__device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32_t max_dwell,
+                                                      const Region &g, uint32_t tid, uint32_t T,
+                                                      uint32_t *s_flag, uint32_t *s_w,
+                                                      uint32_t *w_out, unsigned long long &it)
+{
+    const uint32_t P = perimeter_size(g.w, g.h);
+    const uint32_t lane = tid & 31u;
+    volatile uint32_t *vflag = s_flag;
+    volatile uint32_t *vw = s_w;
+    for (uint32_t base = (tid & ~31u); base < P; base += T) {
+        if (__shfl_sync(kLaneMask, *vflag, 0))
+            break;
+        const uint32_t k = base + lane;
+        const bool active = k < P;
+        const unsigned amask = __ballot_sync(kLaneMask, active);
+        uint32_t px = g.x0, py = g.y0;
+        if (active)
+            perimeter_pixel(g, k, px, py);
+        Orbit o = orbit_start(pixel_c(pm, px, py));
+        bool done = !active;
+        bool differ = false, stop = false;
+        for (;;) {
+            // one value per warp, so every lane uses the same limit
+            const uint32_t wv = __shfl_sync(kLaneMask, *vw, 0);
+            const uint32_t limit = (wv != 0xffffffffu) ? min(max_dwell, wv + 1u) : max_dwell;
+            if (!done)
+                done = orbit_round(o, limit);
+            const unsigned dm = __ballot_sync(kLaneMask, done) & amask;
+            if (dm == amask)
+                break;
+            if (dm) {
+                differ = true;
+                break;
+            }
+            if (__shfl_sync(kLaneMask, *vflag, 0)) {
+                stop = true;
+                break;
+            }
+        }
+        if (active)
+            it += o.d;
+        if (stop)
+            break;
+        if (differ) {
+            if (lane == 0)
+                *vflag = 1u;
+            break;
+        }
+        const uint32_t vmin = __reduce_min_sync(kLaneMask, active ? o.d : 0xffffffffu);
+        const uint32_t vmax = __reduce_max_sync(kLaneMask, active ? o.d : 0u);
+        if (lane == 0) {
+            if (vmin != vmax) {
+                *vflag = 1u;
+            } else {
+                const uint32_t old = atomicCAS(s_w, 0xffffffffu, vmin);
+                if (old != 0xffffffffu && old != vmin)
+                    *vflag = 1u;
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    const bool uniform = (*vflag == 0u);
+    *w_out = *vw;
+    __syncthreads();
+    return uniform;
 }
 
 __device__ __forceinline__ uint32_t ceil_div_u32(uint32_t a, uint32_t b)

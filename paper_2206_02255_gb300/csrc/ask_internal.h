@@ -106,6 +106,7 @@ struct CdpArgs {
     uint32_t max_dwell;
     uint32_t r, B;
     uint32_t count;       // ASK_FLAG_COUNT
+    uint32_t fire_and_forget;  // children into cudaStreamFireAndForget, not the tail stream
     DevCounters *ctr;
 };
 cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, uint32_t by,

@@ -186,43 +186,57 @@ __global__ void __launch_bounds__(256) level_warp_kernel(LevelArgs a, uint32_t o
     for (uint32_t idx = warp; idx < count; idx += nwarps) {
         const uint2 e = a.olt_in[idx];
         const Region g = unpack_region(e);
-        const uint32_t P = perimeter_size(g.w, g.h);
-        uint32_t dmin = 0xffffffffu, dmax = 0u;
-        for (uint32_t k = lane; k < P; k += 32u) {
-            uint32_t px, py;
-            perimeter_pixel(g, k, px, py);
-            const float2 c = pixel_c(a.pm, px, py);
-            const uint32_t d = dwell(c.x, c.y, a.max_dwell);
-            dmin = min(dmin, d);
-            dmax = max(dmax, d);
-            if (k < kWarpStage)
-                stage[k] = d;
-            else
-                a.map[(size_t)py * a.n + px] = d;  // beyond the stage: write through
-            if (COUNT) {
-                it += d;
-                ++bpx;
-            }
-        }
-        dmin = __reduce_min_sync(kFull, dmin);
-        dmax = __reduce_max_sync(kFull, dmax);
         uint32_t kind;
-        if (dmin == dmax) {
-            fill_rect(a.map, a.n, g, dmin, lane, 32u);
-            kind = KIND_FILL;
+        if (a.split) {
+            // only "uniform, and to what" matters: stop at the first difference
+            uint32_t wv = 0;
+            if (warp_perimeter_uniform(a.pm, a.max_dwell, g, lane, &wv, it)) {
+                fill_rect(a.map, a.n, g, wv, lane, 32u);
+                kind = KIND_FILL;
+                if (COUNT && lane == 0)
+                    fpx += (unsigned long long)g.w * g.h;
+            } else {
+                kind = KIND_SPLIT;
+            }
             if (COUNT && lane == 0)
-                fpx += (unsigned long long)g.w * g.h;
-        } else if (a.split) {
-            kind = KIND_SPLIT;
+                bpx += perimeter_size(g.w, g.h);
         } else {
-            // leaf: its perimeter is final, the leaf kernel skips it
-            const uint32_t staged = min(P, kWarpStage);
-            for (uint32_t k = lane; k < staged; k += 32u) {
+            // last level: every perimeter dwell is final (a leaf keeps them)
+            const uint32_t P = perimeter_size(g.w, g.h);
+            uint32_t dmin = 0xffffffffu, dmax = 0u;
+            for (uint32_t k = lane; k < P; k += 32u) {
                 uint32_t px, py;
                 perimeter_pixel(g, k, px, py);
-                a.map[(size_t)py * a.n + px] = stage[k];
+                const float2 c = pixel_c(a.pm, px, py);
+                const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+                dmin = min(dmin, d);
+                dmax = max(dmax, d);
+                if (k < kWarpStage)
+                    stage[k] = d;
+                else
+                    a.map[(size_t)py * a.n + px] = d;  // beyond the stage: write through
+                if (COUNT) {
+                    it += d;
+                    ++bpx;
+                }
             }
-            kind = KIND_LEAF;
+            dmin = __reduce_min_sync(kFull, dmin);
+            dmax = __reduce_max_sync(kFull, dmax);
+            if (dmin == dmax) {
+                fill_rect(a.map, a.n, g, dmin, lane, 32u);
+                kind = KIND_FILL;
+                if (COUNT && lane == 0)
+                    fpx += (unsigned long long)g.w * g.h;
+            } else {
+                // leaf: its perimeter is final, the leaf kernel skips it
+                const uint32_t staged = min(P, kWarpStage);
+                for (uint32_t k = lane; k < staged; k += 32u) {
+                    uint32_t px, py;
+                    perimeter_pixel(g, k, px, py);
+                    a.map[(size_t)py * a.n + px] = stage[k];
+                }
+                kind = KIND_LEAF;
+            }
         }
         if (lane == j) {
             b.rec = e;
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(1024) level_cta_kernel(LevelArgs a, uint32_t o
 {
     extern __shared__ uint32_t stage[];
     __shared__ uint32_t red_min[32], red_max[32];
-    __shared__ uint32_t s_min, s_max, s_base;
+    __shared__ uint32_t s_min, s_max, s_base, s_flag, s_w;
     const uint32_t tid = threadIdx.x, T = blockDim.x, lane = tid & 31u, wid = tid >> 5;
     const uint32_t nw = T >> 5;
     const uint32_t count = min(a.ctr->count[a.level], olt_in_cap);
@@ -273,43 +287,59 @@ __global__ void __launch_bounds__(1024) level_cta_kernel(LevelArgs a, uint32_t o
         const uint2 e = a.olt_in[idx];
         const Region g = unpack_region(e);
         const uint32_t P = perimeter_size(g.w, g.h);
-        uint32_t dmin = 0xffffffffu, dmax = 0u;
-        for (uint32_t k = tid; k < P; k += T) {
-            uint32_t px, py;
-            perimeter_pixel(g, k, px, py);
-            const float2 c = pixel_c(a.pm, px, py);
-            const uint32_t d = dwell(c.x, c.y, a.max_dwell);
-            dmin = min(dmin, d);
-            dmax = max(dmax, d);
-            if (k < stage_cap)
-                stage[k] = d;
-            else
-                a.map[(size_t)py * a.n + px] = d;
-            if (COUNT) {
-                it += d;
-                ++bpx;
+        uint32_t dmin, dmax;
+        if (a.split) {
+            if (tid == 0) {
+                s_flag = 0u;
+                s_w = 0xffffffffu;
             }
-        }
-        dmin = __reduce_min_sync(kFull, dmin);
-        dmax = __reduce_max_sync(kFull, dmax);
-        if (lane == 0) {
-            red_min[wid] = dmin;
-            red_max[wid] = dmax;
-        }
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
-            uint32_t m1 = lane < nw ? red_max[lane] : 0u;
-            m0 = __reduce_min_sync(kFull, m0);
-            m1 = __reduce_max_sync(kFull, m1);
+            __syncthreads();
+            uint32_t wv = 0;
+            const bool uni = cta_perimeter_uniform(a.pm, a.max_dwell, g, tid, T, &s_flag, &s_w, &wv, it);
+            dmin = wv;
+            dmax = uni ? wv : wv + 1u;
+            if (COUNT && tid == 0)
+                bpx += P;
+        } else {
+            dmin = 0xffffffffu;
+            dmax = 0u;
+            for (uint32_t k = tid; k < P; k += T) {
+                uint32_t px, py;
+                perimeter_pixel(g, k, px, py);
+                const float2 c = pixel_c(a.pm, px, py);
+                const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+                dmin = min(dmin, d);
+                dmax = max(dmax, d);
+                if (k < stage_cap)
+                    stage[k] = d;
+                else
+                    a.map[(size_t)py * a.n + px] = d;
+                if (COUNT) {
+                    it += d;
+                    ++bpx;
+                }
+            }
+            dmin = __reduce_min_sync(kFull, dmin);
+            dmax = __reduce_max_sync(kFull, dmax);
             if (lane == 0) {
-                s_min = m0;
-                s_max = m1;
+                red_min[wid] = dmin;
+                red_max[wid] = dmax;
             }
+            __syncthreads();
+            if (wid == 0) {
+                uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
+                uint32_t m1 = lane < nw ? red_max[lane] : 0u;
+                m0 = __reduce_min_sync(kFull, m0);
+                m1 = __reduce_max_sync(kFull, m1);
+                if (lane == 0) {
+                    s_min = m0;
+                    s_max = m1;
+                }
+            }
+            __syncthreads();
+            dmin = s_min;
+            dmax = s_max;
         }
-        __syncthreads();
-        dmin = s_min;
-        dmax = s_max;
         if (dmin == dmax) {
             fill_rect(a.map, a.n, g, dmin, tid, T);
             if (tid == 0) {

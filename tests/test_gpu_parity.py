@@ -101,7 +101,9 @@ def test_ask_c0(ctx, orc, asklib, block):
 
 def test_ask_c0_counters(ctx, orc, asklib):
     """With counting on, pixels and iterations match what the reference's
-    region log implies (the leaf kernel skips perimeters already computed)."""
+    region log implies.  The last level evaluates whole perimeters and the
+    leaf kernel skips them; levels that split stop a perimeter query at the
+    first two dwells that differ, so they make at most the full count."""
     C = inputs.C0
     win, n, M = C["window"], C["n"], C["max_dwell"]
     ex = orc.render_exhaustive(win, n, M)
@@ -111,17 +113,23 @@ def test_ask_c0_counters(ctx, orc, asklib):
     assert np.array_equal(got, want)
     assert st["fill_pixels"] == ost["fill_pixels"]
     assert st["border_pixels"] == ost["border_pixels"]
-    interior_px = interior_it = border_it = 0
+    L = ost["levels"]
+    border_it = [0] * L
+    interior_px = interior_it = 0
     for e in log:
         x0, y0, w, h = (int(e[k]) for k in ("x0", "y0", "w", "h"))
         blk = ex[y0:y0 + h, x0:x0 + w].astype(np.uint64)
         per = blk.sum() - (blk[1:-1, 1:-1].sum() if w > 2 and h > 2 else 0)
-        border_it += int(per)
+        border_it[int(e["level"])] += int(per)
         if e["kind"] == 2 and w > 2 and h > 2:
             interior_px += (w - 2) * (h - 2)
             interior_it += int(blk[1:-1, 1:-1].sum())
     assert st["leaf_pixels"] == interior_px
-    assert st["iterations"] == border_it + interior_it
+    assert st["leaf_iterations"] == interior_it
+    assert st["iterations_per_level"][L - 1] == border_it[L - 1]
+    for i in range(L - 1):
+        assert 0 < st["iterations_per_level"][i] <= border_it[i]
+    assert st["iterations"] == sum(st["iterations_per_level"]) + st["leaf_iterations"]
 
 
 @pytest.mark.parametrize("g,r,B", inputs.c1_sweep())
