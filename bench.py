@@ -31,6 +31,9 @@ if ROOT not in sys.path:
 
 METRIC = "Gpixels/s and dwell-iter/s (ASK vs exhaustive vs CDP2, 1 GB300); p50/p99 latency"
 UNIT = "Gpixels/s"
+# z <- z^2 + c with the library's rounding: fma(-zi, zi, cr), fma(zr, zr, .),
+# zr + zr, fma(., zi, ci); the |z|^2 test is amortised over a block of updates
+FP32_OPS_PER_ITER = 4
 
 
 def parse():
@@ -307,13 +310,15 @@ def run_gpu(args):
         f_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         pass
-    peak = sms * 128 * f_mhz * 1e6 / 6.0 / 1e9             # 6 FP32-pipe ops per iteration
+    # one dwell iteration needs at least 3 FFMA + 1 FADD on the FP32 pipe
+    peak = sms * 128 * f_mhz * 1e6 / FP32_OPS_PER_ITER / 1e9
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "Gdwell-iter/s", "frac": achieved / peak, "traffic": None,
-                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 6 FP32 ops per iteration"
-                              % (sms, f_mhz)}
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / %d FP32 ops per iteration"
+                              % (sms, f_mhz, FP32_OPS_PER_ITER)}
     if clk and clk.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 6.0 / 1e9)
+        roofline["frac_at_sampled_clock"] = achieved / (
+            sms * 128 * clk["sm_mhz"] * 1e6 / FP32_OPS_PER_ITER / 1e9)
 
     # ---- end to end through the C ABI with a host buffer -------------------
     e2e = None

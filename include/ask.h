@@ -81,6 +81,14 @@ typedef enum {
 #define ASK_FLAG_CDP2_FIRE_AND_FORGET 4u /* CDP2: launch children into the fire-and-forget
                                           * stream (concurrent) instead of the tail-launch
                                           * stream (children of one grid run in order) */
+#define ASK_FLAG_EXACT_BORDERS 8u /* ASK: at the last level evaluate every perimeter dwell
+                                   * (staged in shared memory, written to the map) and let
+                                   * the leaf kernel skip perimeters; by default the last
+                                   * level stops at the first two differing dwells and the
+                                   * leaf kernel computes whole leaves */
+#define ASK_FLAG_LEAF_TILED 16u   /* ASK: leaf kernel with one thread per pixel in
+                                   * block_x x block_y tiles instead of the lane-refill
+                                   * kernel (same map) */
 
 typedef struct {
     float re_min, re_max, im_min, im_max;

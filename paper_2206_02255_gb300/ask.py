@@ -22,6 +22,8 @@ METHOD_EXHAUSTIVE, METHOD_ASK, METHOD_CDP2 = 0, 1, 2
 FLAG_COUNT = 1
 FLAG_TIMING = 2
 FLAG_CDP2_FIRE_AND_FORGET = 4
+FLAG_EXACT_BORDERS = 8
+FLAG_LEAF_TILED = 16
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 

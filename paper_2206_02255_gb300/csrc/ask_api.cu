@@ -160,7 +160,8 @@ ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window,
         return set_err(ctx, ASK_EINVAL, "params are required for subdivision methods");
     if (!block_ok(d.block_x, d.block_y))
         return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
-    if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET))
+    if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET |
+                    ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED))
         return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
     if (method != ASK_METHOD_EXHAUSTIVE) {
         if (d.g == 0 || d.g > n)
@@ -463,6 +464,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.olt_cap = (uint32_t)ctx->olt_cap;
         a.leaves = ctx->leaves;
         a.leaf_cap = (uint32_t)ctx->leaf_cap;
+        a.exact_last = (p.flags & ASK_FLAG_EXACT_BORDERS) ? 1u : 0u;
         a.ctr = ctx->ctr;
         // one CTA per region while a level holds too few regions to give
         // every SM several warps, one warp per region below that
@@ -482,8 +484,10 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     la.side = plan.side[L - 1];
     la.leaves = ctx->leaves;
     la.leaf_cap = (uint32_t)ctx->leaf_cap;
+    la.skip_perimeter = (p.flags & ASK_FLAG_EXACT_BORDERS) ? 1u : 0u;
     la.ctr = ctx->ctr;
-    if ((e = launch_leaf(la, p.block_x, p.block_y, count, sms, s)) != cudaSuccess)
+    if ((e = launch_leaf(la, p.block_x, p.block_y, count, (p.flags & ASK_FLAG_LEAF_TILED) != 0, sms,
+                         s)) != cudaSuccess)
         return cuda_err(ctx, e, "leaf kernel");
     ++launches;
     mk.at(2 + (int)L, s);

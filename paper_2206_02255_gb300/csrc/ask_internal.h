@@ -28,6 +28,9 @@ struct DevCounters {
     unsigned long long border_pixels;       // COUNT mode
     unsigned long long level_iters[ASK_MAX_LEVELS];  // COUNT mode: z-updates of level i
     unsigned long long leaf_iters;          // COUNT mode: z-updates of the leaf kernel
+    uint32_t work[ASK_MAX_LEVELS];          // next region a level kernel hands out
+    uint32_t leaf_work;                     // next leaf the leaf kernel hands out
+    uint32_t pad_;
 };
 
 enum : uint32_t {
@@ -79,6 +82,7 @@ struct LevelArgs {
     uint32_t olt_cap;     // capacity of olt_out
     uint2 *leaves;
     uint32_t leaf_cap;
+    uint32_t exact_last;  // last level: evaluate whole perimeters and write them
     DevCounters *ctr;
 };
 // mode: 0 = one warp per region, 1 = one CTA of `threads` per region
@@ -93,10 +97,13 @@ struct LeafArgs {
     uint32_t side;        // nominal side of the leaf regions
     const uint2 *leaves;
     uint32_t leaf_cap;    // capacity of the leaf list
+    uint32_t skip_perimeter;  // leaf perimeters are already in the map
     DevCounters *ctr;
 };
-cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, int sms,
-                        cudaStream_t s);
+// tiled = false: lane-refill kernel (default); true: one thread per pixel in
+// block_x x block_y tiles
+cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, bool tiled,
+                        int sms, cudaStream_t s);
 
 // ---- kernels of ask_cdp2.cu ----------------------------------------------
 struct CdpArgs {

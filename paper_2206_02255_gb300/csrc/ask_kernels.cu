@@ -172,8 +172,6 @@ __global__ void __launch_bounds__(256) level_warp_kernel(LevelArgs a, uint32_t o
     extern __shared__ uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *stage = smem + (threadIdx.x >> 5) * kWarpStage;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t count = min(a.ctr->count[a.level], olt_in_cap);
 
     WarpBatch b;
@@ -183,12 +181,22 @@ __global__ void __launch_bounds__(256) level_warp_kernel(LevelArgs a, uint32_t o
     uint32_t j = 0;
     unsigned long long it = 0, bpx = 0, fpx = 0;
 
-    for (uint32_t idx = warp; idx < count; idx += nwarps) {
+    for (;;) {
+        // regions are handed out one at a time: their costs differ by orders
+        // of magnitude (a uniform perimeter inside the set runs to max_dwell)
+        uint32_t idx = 0;
+        if (lane == 0)
+            idx = atomicAdd(&a.ctr->work[a.level], 1u);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= count)
+            break;
         const uint2 e = a.olt_in[idx];
         const Region g = unpack_region(e);
         uint32_t kind;
-        if (a.split) {
+        if (a.split || !a.exact_last) {
             // only "uniform, and to what" matters: stop at the first difference
+            // (a leaf's pixels, perimeter included, are then all computed by
+            // the leaf kernel)
             uint32_t wv = 0;
             if (warp_perimeter_uniform(a.pm, a.max_dwell, g, lane, &wv, it)) {
                 fill_rect(a.map, a.n, g, wv, lane, 32u);
@@ -196,12 +204,13 @@ __global__ void __launch_bounds__(256) level_warp_kernel(LevelArgs a, uint32_t o
                 if (COUNT && lane == 0)
                     fpx += (unsigned long long)g.w * g.h;
             } else {
-                kind = KIND_SPLIT;
+                kind = a.split ? KIND_SPLIT : KIND_LEAF;
             }
             if (COUNT && lane == 0)
                 bpx += perimeter_size(g.w, g.h);
         } else {
-            // last level: every perimeter dwell is final (a leaf keeps them)
+            // last level, exact perimeters: every perimeter dwell is final (a
+            // leaf keeps them and the leaf kernel skips them)
             const uint32_t P = perimeter_size(g.w, g.h);
             uint32_t dmin = 0xffffffffu, dmax = 0u;
             for (uint32_t k = lane; k < P; k += 32u) {
@@ -277,18 +286,25 @@ __global__ void __launch_bounds__(1024) level_cta_kernel(LevelArgs a, uint32_t o
 {
     extern __shared__ uint32_t stage[];
     __shared__ uint32_t red_min[32], red_max[32];
-    __shared__ uint32_t s_min, s_max, s_base, s_flag, s_w;
+    __shared__ uint32_t s_min, s_max, s_base, s_flag, s_w, s_idx;
     const uint32_t tid = threadIdx.x, T = blockDim.x, lane = tid & 31u, wid = tid >> 5;
     const uint32_t nw = T >> 5;
     const uint32_t count = min(a.ctr->count[a.level], olt_in_cap);
     unsigned long long it = 0, bpx = 0, fpx = 0;
+    const bool query = a.split || !a.exact_last;
 
-    for (uint32_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    for (;;) {
+        if (tid == 0)
+            s_idx = atomicAdd(&a.ctr->work[a.level], 1u);
+        __syncthreads();
+        const uint32_t idx = s_idx;
+        if (idx >= count)
+            break;  // uniform over the CTA
         const uint2 e = a.olt_in[idx];
         const Region g = unpack_region(e);
         const uint32_t P = perimeter_size(g.w, g.h);
         uint32_t dmin, dmax;
-        if (a.split) {
+        if (query) {
             if (tid == 0) {
                 s_flag = 0u;
                 s_w = 0xffffffffu;
@@ -362,11 +378,13 @@ __global__ void __launch_bounds__(1024) level_cta_kernel(LevelArgs a, uint32_t o
                     atomicOr(&a.ctr->error, ERR_OLT_OVERFLOW);
             }
         } else {
-            const uint32_t staged = min(P, stage_cap);
-            for (uint32_t k = tid; k < staged; k += T) {
-                uint32_t px, py;
-                perimeter_pixel(g, k, px, py);
-                a.map[(size_t)py * a.n + px] = stage[k];
+            if (!query) {
+                const uint32_t staged = min(P, stage_cap);
+                for (uint32_t k = tid; k < staged; k += T) {
+                    uint32_t px, py;
+                    perimeter_pixel(g, k, px, py);
+                    a.map[(size_t)py * a.n + px] = stage[k];
+                }
             }
             if (tid == 0) {
                 const uint32_t slot = atomicAdd(&a.ctr->leaf_count, 1u);
@@ -378,6 +396,7 @@ __global__ void __launch_bounds__(1024) level_cta_kernel(LevelArgs a, uint32_t o
         }
         __syncthreads();  // the stage and s_* are reused by the next region
     }
+    __syncthreads();
     if (COUNT) {
         it = warp_sum_u64(it);
         bpx = warp_sum_u64(bpx);
@@ -414,7 +433,7 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
         const uint32_t ty = t / tiles_x, tx = t - ty * tiles_x;
         const uint32_t px = g.x0 + tx * blockDim.x + threadIdx.x;
         const uint32_t py = g.y0 + ty * blockDim.y + threadIdx.y;
-        if (px < g.x0 + g.w && py < g.y0 + g.h && !on_perimeter(g, px, py)) {
+        if (px < g.x0 + g.w && py < g.y0 + g.h && !(a.skip_perimeter && on_perimeter(g, px, py))) {
             const float2 c = pixel_c(a.pm, px, py);
             const uint32_t d = dwell(c.x, c.y, a.max_dwell);
             a.map[(size_t)py * a.n + px] = d;
@@ -428,6 +447,197 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
         it = warp_sum_u64(it);
         lpx = warp_sum_u64(lpx);
         if ((threadIdx.x + threadIdx.y * blockDim.x) % 32u == 0u) {
+            if (it) {
+                atomicAdd(&a.ctr->iterations, it);
+                atomicAdd(&a.ctr->leaf_iters, it);
+            }
+            if (lpx)
+                atomicAdd(&a.ctr->leaf_pixels, lpx);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf kernel with lane refill.  Leaf pixels near the set's boundary have
+// dwells from a handful of updates to max_dwell side by side, so a warp that
+// owned 32 fixed pixels would idle most lanes while one orbit runs on.  Here
+// each warp takes leaves from a device counter and feeds their pixels to its
+// lanes one at a time:
+//  * every round, each busy lane advances its orbit by one unchecked block
+//    (see dwell()); a lane whose block ends escaped, or that has fewer than a
+//    block's worth of updates left, parks (saved state, count, pixel) in the
+//    warp's replay buffer in shared memory and takes a new pixel at once;
+//  * when 32 orbits are parked, the warp replays them together, one per
+//    lane, with a tested update per step (at most one block each), and
+//    writes their dwells.
+// Lanes stay busy until the warp runs out of leaves.
+// ---------------------------------------------------------------------------
+constexpr int kRefillWarps = 8;   // warps per CTA
+constexpr uint32_t kParkCap = 64; // parked orbits per warp (< 32 + 32)
+
+template <bool COUNT>
+__device__ __forceinline__ void replay_parked(const LeafArgs &a, float4 f, uint2 u,
+                                              unsigned long long &it)
+{
+    float x = f.x, y = f.y;
+    const float cr = f.z, ci = f.w;
+    uint32_t d = u.x;
+    while (d < a.max_dwell && z_bounded(x, y)) {
+        z_update(x, y, cr, ci);
+        ++d;
+    }
+    const uint32_t px = u.y & 0xffffu, py = u.y >> 16;
+    a.map[(size_t)py * a.n + px] = d;
+    if (COUNT)
+        it += d;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs a)
+{
+    __shared__ float4 park_f[kRefillWarps][kParkCap];  // saved x, y and c
+    __shared__ uint2 park_u[kRefillWarps][kParkCap];   // count, pixel (py << 16 | px)
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    float4 *qf = park_f[wib];
+    uint2 *qu = park_u[wib];
+    uint32_t parked = 0;  // warp-uniform
+
+    const uint32_t nleaves = min(a.ctr->leaf_count, a.leaf_cap);
+    const uint32_t K = (uint32_t)kUnroll;
+    // the warp's current leaf: the part still to hand out, as a row-major cursor
+    Region g;
+    g.x0 = g.y0 = 0;
+    g.w = g.h = 1;
+    uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1;
+    bool more = true;
+    // this lane's orbit
+    bool busy = false, fast = false;
+    float x = 0.0f, y = 0.0f, cr = 0.0f, ci = 0.0f;
+    uint32_t d = 0, pix = 0;
+    unsigned long long it = 0, lpx = 0;
+
+    for (;;) {
+        // ---- refill idle lanes
+        unsigned idle = __ballot_sync(kFull, !busy);
+        while (idle && more) {
+            if (rem == 0) {
+                uint32_t li = 0;
+                if (lane == 0)
+                    li = atomicAdd(&a.ctr->leaf_work, 1u);
+                li = __shfl_sync(kFull, li, 0);
+                if (li >= nleaves) {
+                    more = false;
+                    break;
+                }
+                g = unpack_region(a.leaves[li]);
+                if (a.skip_perimeter) {
+                    // only the interior; a leaf of side <= 2 is all perimeter
+                    cw = g.w > 2u ? g.w - 2u : 0u;
+                    rem = (g.w > 2u && g.h > 2u) ? cw * (g.h - 2u) : 0u;
+                    ox = g.x0 + 1u;
+                    oy = g.y0 + 1u;
+                } else {
+                    cw = g.w;
+                    rem = g.w * g.h;
+                    ox = g.x0;
+                    oy = g.y0;
+                }
+                row0 = col0 = 0;
+                continue;
+            }
+            const uint32_t nidle = (uint32_t)__popc(idle);
+            const uint32_t take = min(nidle, rem);
+            const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
+            if (!busy && rank < take) {
+                uint32_t col = col0 + rank, row = row0;
+                while (col >= cw) {
+                    col -= cw;
+                    ++row;
+                }
+                const uint32_t px = ox + col, py = oy + row;
+                const float2 c = pixel_c(a.pm, px, py);
+                cr = c.x;
+                ci = c.y;
+                x = 0.0f;
+                y = 0.0f;
+                d = 0;
+                pix = (py << 16) | px;
+                fast = escape_absorbing(cr, ci);
+                busy = true;
+            }
+            col0 += take;
+            while (col0 >= cw) {
+                col0 -= cw;
+                ++row0;
+            }
+            rem -= take;
+            idle = __ballot_sync(kFull, !busy);
+        }
+        if (!__any_sync(kFull, busy))
+            break;
+
+        // ---- one unchecked block per busy lane
+        bool park = false;
+        float sx = x, sy = y;
+        if (busy) {
+            if (fast && a.max_dwell - d >= K) {
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k)
+                    z_update(x, y, cr, ci);
+                if (z_bounded(x, y)) {
+                    d += K;
+                } else {
+                    park = true;  // escaped inside this block: replay it
+                }
+            } else {
+                park = true;      // tail below max_dwell, or |c| near 2
+            }
+        }
+
+        // ---- park finished orbits; replay 32 at a time
+        const unsigned pmask = __ballot_sync(kFull, park);
+        if (pmask) {
+            if (park) {
+                const uint32_t slot = parked + (uint32_t)__popc(pmask & lt_mask);
+                qf[slot] = make_float4(sx, sy, cr, ci);
+                qu[slot] = make_uint2(d, pix);
+                busy = false;
+            }
+            parked += (uint32_t)__popc(pmask);
+            __syncwarp();
+            if (parked >= 32u) {
+                const float4 f = qf[lane];
+                const uint2 u = qu[lane];
+                float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint2 u2 = make_uint2(0u, 0u);
+                if (lane < parked - 32u) {
+                    f2 = qf[32u + lane];
+                    u2 = qu[32u + lane];
+                }
+                __syncwarp();
+                if (lane < parked - 32u) {
+                    qf[lane] = f2;
+                    qu[lane] = u2;
+                }
+                parked -= 32u;
+                __syncwarp();
+                replay_parked<COUNT>(a, f, u, it);
+                if (COUNT)
+                    ++lpx;
+            }
+        }
+    }
+    // ---- the orbits still parked
+    if (lane < parked) {
+        replay_parked<COUNT>(a, qf[lane], qu[lane], it);
+        if (COUNT)
+            ++lpx;
+    }
+    if (COUNT) {
+        it = warp_sum_u64(it);
+        lpx = warp_sum_u64(lpx);
+        if (lane == 0) {
             if (it) {
                 atomicAdd(&a.ctr->iterations, it);
                 atomicAdd(&a.ctr->leaf_iters, it);
@@ -515,9 +725,20 @@ cudaError_t launch_level(const LevelArgs &a, int mode, uint32_t threads, bool co
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, int sms,
-                        cudaStream_t s)
+cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, bool tiled,
+                        int sms, cudaStream_t s)
 {
+    if (!tiled) {
+        const int threads = kRefillWarps * 32;
+        if (count) {
+            const int grid = persistent_grid(leaf_refill_kernel<true>, threads, 0, sms);
+            leaf_refill_kernel<true><<<grid, threads, 0, s>>>(a);
+        } else {
+            const int grid = persistent_grid(leaf_refill_kernel<false>, threads, 0, sms);
+            leaf_refill_kernel<false><<<grid, threads, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
     const uint32_t tiles_x = (a.side + bx - 1) / bx, tiles_y = (a.side + by - 1) / by;
     const dim3 block(bx, by);
     const int threads = (int)(bx * by);

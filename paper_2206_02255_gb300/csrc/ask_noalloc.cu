@@ -219,6 +219,7 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
         a.olt_cap = kNoAllocRegions;
         a.leaves = sc->leaves;
         a.leaf_cap = kNoAllocRegions;
+        a.exact_last = 0u;
         a.ctr = sc->ctr;
         const uint64_t warp_slots = (uint64_t)sc->sms * 16u;
         const int mode = (plan.max_regions[i] < warp_slots && plan.side[i] >= 64u) ? 1 : 0;
@@ -234,8 +235,9 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
     la.side = plan.side[L - 1];
     la.leaves = sc->leaves;
     la.leaf_cap = kNoAllocRegions;
+    la.skip_perimeter = 0u;
     la.ctr = sc->ctr;
-    if (launch_leaf(la, p.block_x, p.block_y, false, sc->sms, s) != cudaSuccess)
+    if (launch_leaf(la, p.block_x, p.block_y, false, false, sc->sms, s) != cudaSuccess)
         return ASK_ECUDA;
     return ASK_OK;
 }

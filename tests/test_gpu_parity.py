@@ -99,37 +99,62 @@ def test_ask_c0(ctx, orc, asklib, block):
               C["B"], block)
 
 
-def test_ask_c0_counters(ctx, orc, asklib):
+@pytest.mark.parametrize("exact", [False, True], ids=["query", "exact_borders"])
+def test_ask_c0_counters(ctx, orc, asklib, exact):
     """With counting on, pixels and iterations match what the reference's
-    region log implies.  The last level evaluates whole perimeters and the
-    leaf kernel skips them; levels that split stop a perimeter query at the
-    first two dwells that differ, so they make at most the full count."""
+    region log implies.  Perimeter queries stop at the first two dwells that
+    differ, so a level makes at most the full perimeter count; with exact
+    borders the last level evaluates whole perimeters and the leaf kernel
+    skips them, otherwise the leaf kernel computes whole leaves."""
     C = inputs.C0
     win, n, M = C["window"], C["n"], C["max_dwell"]
     ex = orc.render_exhaustive(win, n, M)
     want, ost, log = orc.render_ms(win, n, M, C["g"], C["r"], C["B"], log=True)
-    got, st = gpu_map(ctx, "ask", win, n, M, params(asklib, C["g"], C["r"], C["B"], count=True),
-                      stats=True)
+    p = params(asklib, C["g"], C["r"], C["B"], count=True)
+    if exact:
+        p.flags |= asklib.FLAG_EXACT_BORDERS
+    got, st = gpu_map(ctx, "ask", win, n, M, p, stats=True)
     assert np.array_equal(got, want)
     assert st["fill_pixels"] == ost["fill_pixels"]
     assert st["border_pixels"] == ost["border_pixels"]
     L = ost["levels"]
     border_it = [0] * L
-    interior_px = interior_it = 0
+    leaf_px = leaf_it = 0
     for e in log:
         x0, y0, w, h = (int(e[k]) for k in ("x0", "y0", "w", "h"))
         blk = ex[y0:y0 + h, x0:x0 + w].astype(np.uint64)
-        per = blk.sum() - (blk[1:-1, 1:-1].sum() if w > 2 and h > 2 else 0)
-        border_it[int(e["level"])] += int(per)
-        if e["kind"] == 2 and w > 2 and h > 2:
-            interior_px += (w - 2) * (h - 2)
-            interior_it += int(blk[1:-1, 1:-1].sum())
-    assert st["leaf_pixels"] == interior_px
-    assert st["leaf_iterations"] == interior_it
-    assert st["iterations_per_level"][L - 1] == border_it[L - 1]
-    for i in range(L - 1):
+        inner = blk[1:-1, 1:-1] if w > 2 and h > 2 else blk[:0, :0]
+        border_it[int(e["level"])] += int(blk.sum() - inner.sum())
+        if e["kind"] == 2:
+            if exact:
+                leaf_px += inner.size
+                leaf_it += int(inner.sum())
+            else:
+                leaf_px += blk.size
+                leaf_it += int(blk.sum())
+    assert st["leaf_pixels"] == leaf_px
+    assert st["leaf_iterations"] == leaf_it
+    if exact:
+        assert st["iterations_per_level"][L - 1] == border_it[L - 1]
+    for i in range(L):
         assert 0 < st["iterations_per_level"][i] <= border_it[i]
     assert st["iterations"] == sum(st["iterations_per_level"]) + st["leaf_iterations"]
+
+
+@pytest.mark.parametrize("flags", ["EXACT_BORDERS", "LEAF_TILED", "EXACT_BORDERS|LEAF_TILED"])
+def test_ask_flag_variants(ctx, orc, asklib, flags):
+    """The last-level and leaf-kernel variants give the same map."""
+    f = 0
+    for name in flags.split("|"):
+        f |= getattr(asklib, "FLAG_" + name)
+    for win, n, M, g, r, B, block in [(inputs.WINDOW_PAPER, 1024, 512, 16, 2, 32, (16, 16)),
+                                      (inputs.WINDOW_WIDE, 777, 300, 5, 3, 4, (8, 8)),
+                                      (inputs.WINDOW_PAPER, 2048, 2048, 32, 4, 16, (32, 8))]:
+        want, _ = orc.render_ms(win, n, M, g, r, B)
+        p = params(asklib, g, r, B, block)
+        p.flags = f
+        got = gpu_map(ctx, "ask", win, n, M, p)
+        assert first_diff(got, want) is None, (flags, n, g, r, B, first_diff(got, want))
 
 
 @pytest.mark.parametrize("g,r,B", inputs.c1_sweep())
