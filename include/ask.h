@@ -119,6 +119,7 @@ typedef struct {
     float ms_total;                            /* device time of the render */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: device time of level kernel i */
     float ms_leaf;                             /* ASK: device time of the leaf kernel */
+    float ms_fill;                             /* ASK: device time of the deferred-fill kernel */
     uint32_t kernel_launches;                  /* kernels this render launched from the host */
 } ask_stats;
 
@@ -133,6 +134,7 @@ typedef struct {
     float ms_init;                             /* ASK: init kernel */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: level kernel i */
     float ms_leaf;                             /* ASK: leaf kernel */
+    float ms_fill;                             /* ASK: deferred-fill kernel */
 } ask_timing;
 
 typedef struct ask_ctx ask_ctx;

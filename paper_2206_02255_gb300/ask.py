@@ -50,7 +50,7 @@ class Stats(ctypes.Structure):
                 ("iterations_per_level", ctypes.c_uint64 * ASK_MAX_LEVELS),
                 ("leaf_iterations", ctypes.c_uint64), ("ms_total", ctypes.c_float),
                 ("ms_per_level", ctypes.c_float * ASK_MAX_LEVELS), ("ms_leaf", ctypes.c_float),
-                ("kernel_launches", ctypes.c_uint32)]
+                ("ms_fill", ctypes.c_float), ("kernel_launches", ctypes.c_uint32)]
 
     def as_dict(self):
         L = self.levels
@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
             "iterations_per_level": list(self.iterations_per_level[:L]),
             "leaf_iterations": self.leaf_iterations, "ms_total": self.ms_total,
             "ms_per_level": list(self.ms_per_level[:L]), "ms_leaf": self.ms_leaf,
-            "kernel_launches": self.kernel_launches,
+            "ms_fill": self.ms_fill, "kernel_launches": self.kernel_launches,
         }
 
 
@@ -73,13 +73,15 @@ class Timing(ctypes.Structure):
     _fields_ = [("renders", ctypes.c_uint32), ("dropped", ctypes.c_uint32),
                 ("levels", ctypes.c_uint32), ("method", ctypes.c_uint32),
                 ("ms_total", ctypes.c_float), ("ms_init", ctypes.c_float),
-                ("ms_per_level", ctypes.c_float * ASK_MAX_LEVELS), ("ms_leaf", ctypes.c_float)]
+                ("ms_per_level", ctypes.c_float * ASK_MAX_LEVELS), ("ms_leaf", ctypes.c_float),
+                ("ms_fill", ctypes.c_float)]
 
     def as_dict(self):
         L = self.levels
         return {"renders": self.renders, "dropped": self.dropped, "levels": L,
                 "method": self.method, "ms_total": self.ms_total, "ms_init": self.ms_init,
-                "ms_per_level": list(self.ms_per_level[:L]), "ms_leaf": self.ms_leaf}
+                "ms_per_level": list(self.ms_per_level[:L]), "ms_leaf": self.ms_leaf,
+                "ms_fill": self.ms_fill}
 
 
 class AskError(RuntimeError):

@@ -19,6 +19,10 @@ struct ask_ctx {
     uint64_t olt_cap = 0;
     uint2 *leaves = nullptr;
     uint64_t leaf_cap = 0;
+    uint4 *rst[2] = {nullptr, nullptr};  // per-region state of chunked queries
+    uint64_t rst_cap = 0;
+    uint4 *fills = nullptr;              // deferred fills
+    uint64_t fill_cap = 0;
     ask::DevCounters *ctr = nullptr;
     ask::DevCounters *h_ctr = nullptr;  // pinned mirror for stats
     // device map for ask_render_host
@@ -26,11 +30,11 @@ struct ask_ctx {
     size_t dmap_elems = 0;
     // events of the synchronous stats path: 0 = start, 1 = after init,
     // 2 + i = after level i, levels + 2 = after the leaf kernel
-    cudaEvent_t ev[ASK_MAX_LEVELS + 3];
+    cudaEvent_t ev[ASK_MAX_LEVELS + 4];
     bool events = false;
     // ASK_FLAG_TIMING: a ring of per-render event sets, read by ask_timing_read
     struct TimingSlot {
-        cudaEvent_t ev[ASK_MAX_LEVELS + 3];
+        cudaEvent_t ev[ASK_MAX_LEVELS + 4];
         uint32_t levels;
         uint32_t method;
     };
@@ -51,6 +55,7 @@ bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
     if (n == 0 || g == 0 || r < 2 || B == 0 || !plan)
         return false;
     std::memset(plan, 0, sizeof(*plan));
+    // (levels are capped below ASK_MAX_LEVELS so event arrays have room)
     uint32_t s = ceil_div(n, g);
     // multiset of interval lengths along one axis: (length, how many)
     std::vector<std::pair<uint32_t, uint64_t>> lens;
@@ -61,7 +66,7 @@ bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
         lens.push_back({rem, 1});
     plan->axis0 = full + (rem ? 1u : 0u);
     for (uint32_t i = 0;; ++i) {
-        if (i >= ASK_MAX_LEVELS)
+        if (i >= ASK_MAX_LEVELS - 2)
             return false;
         uint64_t axis = 0;
         for (auto &p : lens)
@@ -69,6 +74,10 @@ bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
         plan->side[i] = s;
         plan->max_regions[i] = axis * axis;
         if (plan->max_regions[i] >= 0xffffffffull)
+            return false;
+        const uint64_t per = (s <= 2u) ? (uint64_t)s * s : 4ull * s - 4ull;
+        plan->chunks[i] = (uint32_t)((per + kChunkPx - 1) / kChunkPx);
+        if (plan->max_regions[i] * plan->chunks[i] >= 0xffffffffull)
             return false;
         const uint32_t sc = ceil_div(s, r);
         plan->split[i] = (s > 1u && sc >= B) ? 1u : 0u;
@@ -205,37 +214,65 @@ ask_status ensure_counters(ask_ctx *ctx)
     return ASK_OK;
 }
 
+template <typename T>
+ask_status grow(ask_ctx *ctx, T **buf, uint64_t *cap, uint64_t need, const char *what)
+{
+    if (need <= *cap)
+        return ASK_OK;
+    if (*buf)
+        cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(buf, need * sizeof(T));
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, what);
+    *cap = need;
+    return ASK_OK;
+}
+
+// Deferred fills can come from levels whose regions exceed the in-place size.
+uint64_t fill_need(const LevelPlan &plan)
+{
+    uint64_t need = 0;
+    for (uint32_t i = 0; i < plan.levels; ++i)
+        if ((uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
+            need += plan.max_regions[i];
+    return need;
+}
+
 ask_status reserve_ask(ask_ctx *ctx, const LevelPlan &plan)
 {
-    uint64_t olt_need = 0;
-    for (uint32_t i = 0; i < plan.levels; ++i)
+    uint64_t olt_need = 0, rst_need = 0;
+    for (uint32_t i = 0; i < plan.levels; ++i) {
         if (plan.max_regions[i] > olt_need)
             olt_need = plan.max_regions[i];
+        if (plan.chunks[i] > 1u && plan.max_regions[i] > rst_need)
+            rst_need = plan.max_regions[i];
+    }
     const uint64_t leaf_need = plan.max_regions[plan.levels - 1];
+    ask_status st;
     if (olt_need > ctx->olt_cap) {
-        for (int b = 0; b < 2; ++b) {
-            if (ctx->olt[b])
-                cudaFree(ctx->olt[b]);
-            ctx->olt[b] = nullptr;
-        }
-        ctx->olt_cap = 0;
-        for (int b = 0; b < 2; ++b) {
-            cudaError_t e = cudaMalloc(&ctx->olt[b], olt_need * sizeof(uint2));
-            if (e != cudaSuccess)
-                return cuda_err(ctx, e, "cudaMalloc(region table)");
+        uint64_t c0 = ctx->olt_cap, c1 = ctx->olt_cap;
+        if ((st = grow(ctx, &ctx->olt[0], &c0, olt_need, "cudaMalloc(region table)")) != ASK_OK ||
+            (st = grow(ctx, &ctx->olt[1], &c1, olt_need, "cudaMalloc(region table)")) != ASK_OK) {
+            ctx->olt_cap = 0;
+            return st;
         }
         ctx->olt_cap = olt_need;
     }
-    if (leaf_need > ctx->leaf_cap) {
-        if (ctx->leaves)
-            cudaFree(ctx->leaves);
-        ctx->leaves = nullptr;
-        ctx->leaf_cap = 0;
-        cudaError_t e = cudaMalloc(&ctx->leaves, leaf_need * sizeof(uint2));
-        if (e != cudaSuccess)
-            return cuda_err(ctx, e, "cudaMalloc(leaf list)");
-        ctx->leaf_cap = leaf_need;
+    if (rst_need > ctx->rst_cap) {
+        uint64_t c0 = ctx->rst_cap, c1 = ctx->rst_cap;
+        if ((st = grow(ctx, &ctx->rst[0], &c0, rst_need, "cudaMalloc(query state)")) != ASK_OK ||
+            (st = grow(ctx, &ctx->rst[1], &c1, rst_need, "cudaMalloc(query state)")) != ASK_OK) {
+            ctx->rst_cap = 0;
+            return st;
+        }
+        ctx->rst_cap = rst_need;
     }
+    if ((st = grow(ctx, &ctx->leaves, &ctx->leaf_cap, leaf_need, "cudaMalloc(leaf list)")) != ASK_OK)
+        return st;
+    if ((st = grow(ctx, &ctx->fills, &ctx->fill_cap, fill_need(plan), "cudaMalloc(fill list)")) != ASK_OK)
+        return st;
     return ensure_counters(ctx);
 }
 
@@ -243,7 +280,7 @@ ask_status ensure_events(ask_ctx *ctx)
 {
     if (ctx->events)
         return ASK_OK;
-    for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i) {
+    for (int i = 0; i < ASK_MAX_LEVELS + 4; ++i) {
         cudaError_t e = cudaEventCreate(&ctx->ev[i]);
         if (e != cudaSuccess)
             return cuda_err(ctx, e, "cudaEventCreate");
@@ -292,7 +329,7 @@ ask_status ensure_ring(ask_ctx *ctx)
     for (uint32_t k = 0; k < ask_ctx::kRing; ++k) {
         ring[k].levels = 0;
         ring[k].method = 0;
-        for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i) {
+        for (int i = 0; i < ASK_MAX_LEVELS + 4; ++i) {
             cudaError_t e = cudaEventCreate(&ring[k].ev[i]);
             if (e != cudaSuccess) {
                 delete[] ring;
@@ -354,7 +391,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     if (method == ASK_METHOD_EXHAUSTIVE) {
         mk.at(0, s);
         if (count) {
-            if ((e = launch_init(nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
+            if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
                 return cuda_err(ctx, e, "init kernel");
             ++launches;
         }
@@ -403,7 +440,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
             cudaGetLastError();  // a refused raise is not sticky
         }
         mk.at(0, s);
-        if ((e = launch_init(nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
+        if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
             return cuda_err(ctx, e, "init kernel");
         CdpArgs a;
         a.map = d_dwell;
@@ -438,13 +475,15 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         return ASK_OK;
     }
 
-    // ---- ASK: init, one level kernel per depth, leaf kernel ---------------
+    // ---- ASK: init, one level kernel per depth, fills, leaf kernel --------
     if ((st = reserve_ask(ctx, plan)) != ASK_OK)
         return st;
     const int sms = ctx->dev.sms;
     const uint32_t L = plan.levels;
+    const bool exact = (p.flags & ASK_FLAG_EXACT_BORDERS) != 0;
     mk.at(0, s);
-    if ((e = launch_init(ctx->olt[0], ctx->ctr, n, plan.side[0], plan.axis0, s)) != cudaSuccess)
+    if ((e = launch_init(ctx->olt[0], plan.chunks[0] > 1u ? ctx->rst[0] : nullptr, ctx->ctr, n,
+                         plan.side[0], plan.axis0, s)) != cudaSuccess)
         return cuda_err(ctx, e, "init kernel");
     ++launches;
     mk.at(1, s);
@@ -462,20 +501,34 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.olt_in = ctx->olt[i & 1];
         a.olt_out = ctx->olt[(i + 1) & 1];
         a.olt_cap = (uint32_t)ctx->olt_cap;
+        a.chunks = plan.chunks[i];
+        a.next_chunks = (i + 1 < L) ? plan.chunks[i + 1] : 1u;
+        a.rst_in = ctx->rst[i & 1];
+        a.rst_out = ctx->rst[(i + 1) & 1];
         a.leaves = ctx->leaves;
         a.leaf_cap = (uint32_t)ctx->leaf_cap;
-        a.exact_last = (p.flags & ASK_FLAG_EXACT_BORDERS) ? 1u : 0u;
+        a.fills = ctx->fill_cap ? ctx->fills : nullptr;
+        a.fill_cap = (uint32_t)ctx->fill_cap;
+        a.exact_last = exact ? 1u : 0u;
         a.ctr = ctx->ctr;
-        // one CTA per region while a level holds too few regions to give
-        // every SM several warps, one warp per region below that
-        const uint64_t warp_slots = (uint64_t)sms * 16u;
-        const int mode = (plan.max_regions[i] < warp_slots && plan.side[i] >= 64u) ? 1 : 0;
-        const uint32_t threads = plan.side[i] >= 1024u ? 512u : 256u;
-        if ((e = launch_level(a, mode, threads, count, sms, s)) != cudaSuccess)
+        if ((e = launch_level(a, count, sms, s)) != cudaSuccess)
             return cuda_err(ctx, e, "level kernel");
         ++launches;
         mk.at(2 + (int)i, s);
     }
+    if (fill_need(plan) > 0) {
+        FillArgs f;
+        f.map = d_dwell;
+        f.n = n;
+        f.fills = ctx->fills;
+        f.fill_cap = (uint32_t)ctx->fill_cap;
+        f.max_rows = plan.side[0];
+        f.ctr = ctx->ctr;
+        if ((e = launch_fill(f, sms, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "fill kernel");
+        ++launches;
+    }
+    mk.at(2 + (int)L, s);
     LeafArgs la;
     la.map = d_dwell;
     la.n = n;
@@ -484,13 +537,13 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     la.side = plan.side[L - 1];
     la.leaves = ctx->leaves;
     la.leaf_cap = (uint32_t)ctx->leaf_cap;
-    la.skip_perimeter = (p.flags & ASK_FLAG_EXACT_BORDERS) ? 1u : 0u;
+    la.skip_perimeter = exact ? 1u : 0u;
     la.ctr = ctx->ctr;
     if ((e = launch_leaf(la, p.block_x, p.block_y, count, (p.flags & ASK_FLAG_LEAF_TILED) != 0, sms,
                          s)) != cudaSuccess)
         return cuda_err(ctx, e, "leaf kernel");
     ++launches;
-    mk.at(2 + (int)L, s);
+    mk.at(3 + (int)L, s);
     if (timing) {
         slot->levels = L;
         ++ctx->ring_head;
@@ -498,10 +551,11 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     if (stats) {
         if ((st = read_counters(ctx, s)) != ASK_OK)
             return st;
-        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[L + 2]);
+        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[L + 3]);
         for (uint32_t i = 0; i < L; ++i)
             cudaEventElapsedTime(&stats->ms_per_level[i], ctx->ev[i + 1], ctx->ev[i + 2]);
-        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 1], ctx->ev[L + 2]);
+        cudaEventElapsedTime(&stats->ms_fill, ctx->ev[L + 1], ctx->ev[L + 2]);
+        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 2], ctx->ev[L + 3]);
         const DevCounters &c = *ctx->h_ctr;
         stats->levels = L;
         for (uint32_t i = 0; i < L; ++i) {
@@ -581,6 +635,11 @@ void ask_ctx_destroy(ask_ctx *ctx)
             cudaFree(ctx->olt[b]);
     if (ctx->leaves)
         cudaFree(ctx->leaves);
+    for (int b = 0; b < 2; ++b)
+        if (ctx->rst[b])
+            cudaFree(ctx->rst[b]);
+    if (ctx->fills)
+        cudaFree(ctx->fills);
     if (ctx->ctr)
         cudaFree(ctx->ctr);
     if (ctx->h_ctr)
@@ -588,11 +647,11 @@ void ask_ctx_destroy(ask_ctx *ctx)
     if (ctx->dmap)
         cudaFree(ctx->dmap);
     if (ctx->events)
-        for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i)
+        for (int i = 0; i < ASK_MAX_LEVELS + 4; ++i)
             cudaEventDestroy(ctx->ev[i]);
     if (ctx->ring) {
         for (uint32_t k = 0; k < ask_ctx::kRing; ++k)
-            for (int i = 0; i < ASK_MAX_LEVELS + 3; ++i)
+            for (int i = 0; i < ASK_MAX_LEVELS + 4; ++i)
                 cudaEventDestroy(ctx->ring[k].ev[i]);
         delete[] ctx->ring;
     }
@@ -704,7 +763,7 @@ ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
     for (uint64_t k = ctx->ring_tail; k < ctx->ring_head; ++k) {
         const ask_ctx::TimingSlot &sl = ctx->ring[k % ask_ctx::kRing];
         const uint32_t L = sl.levels;
-        const int last = (sl.method == ASK_METHOD_ASK) ? (int)L + 2 : 1;
+        const int last = (sl.method == ASK_METHOD_ASK) ? (int)L + 3 : 1;
         float ms = 0.0f;
         if ((e = cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[last])) != cudaSuccess)
             return cuda_err(ctx, e, "cudaEventElapsedTime");
@@ -717,6 +776,8 @@ ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
                 out->ms_per_level[i] += ms;
             }
             cudaEventElapsedTime(&ms, sl.ev[L + 1], sl.ev[L + 2]);
+            out->ms_fill += ms;
+            cudaEventElapsedTime(&ms, sl.ev[L + 2], sl.ev[L + 3]);
             out->ms_leaf += ms;
         }
         out->levels = L;

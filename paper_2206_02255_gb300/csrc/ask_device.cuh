@@ -207,23 +207,27 @@ __device__ __forceinline__ bool on_perimeter(const Region &g, uint32_t px, uint3
 __device__ __forceinline__ void fill_rect(uint32_t *__restrict__ map, uint32_t n, const Region &g,
                                           uint32_t v, uint32_t t, uint32_t nthr)
 {
-    const uint32_t chunks_per_row = (g.w + 3u) / 4u + 1u;  // upper bound for any alignment
-    const uint32_t items = chunks_per_row * g.h;
+    const uint32_t cpr = (g.w + 3u) / 4u + 1u;  // chunks per row, an upper bound for any alignment
     const uint4 v4 = make_uint4(v, v, v, v);
-    for (uint32_t it = t; it < items; it += nthr) {
-        const uint32_t row = it / chunks_per_row, c = it - row * chunks_per_row;
+    uint32_t row = t / cpr, c = t - row * cpr;   // then advanced without dividing
+    while (row < g.h) {
         const size_t start = (size_t)(g.y0 + row) * n + g.x0;
         const size_t end = start + g.w;
         const size_t e0 = ((start >> 2) + c) << 2;
-        if (e0 >= end)
-            continue;
-        if (e0 >= start && e0 + 4u <= end) {
-            *reinterpret_cast<uint4 *>(map + e0) = v4;
-        } else {
+        if (e0 < end) {
+            if (e0 >= start && e0 + 4u <= end) {
+                *reinterpret_cast<uint4 *>(map + e0) = v4;
+            } else {
 #pragma unroll
-            for (uint32_t k = 0; k < 4u; ++k)
-                if (e0 + k >= start && e0 + k < end)
-                    map[e0 + k] = v;
+                for (uint32_t k = 0; k < 4u; ++k)
+                    if (e0 + k >= start && e0 + k < end)
+                        map[e0 + k] = v;
+            }
+        }
+        c += nthr;
+        while (c >= cpr) {
+            c -= cpr;
+            ++row;
         }
     }
 }

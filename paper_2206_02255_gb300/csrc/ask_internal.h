@@ -28,8 +28,10 @@ struct DevCounters {
     unsigned long long border_pixels;       // COUNT mode
     unsigned long long level_iters[ASK_MAX_LEVELS];  // COUNT mode: z-updates of level i
     unsigned long long leaf_iters;          // COUNT mode: z-updates of the leaf kernel
-    uint32_t work[ASK_MAX_LEVELS];          // next region a level kernel hands out
+    uint32_t work[ASK_MAX_LEVELS];          // next work item a level kernel hands out
     uint32_t leaf_work;                     // next leaf the leaf kernel hands out
+    uint32_t fill_count;                    // entries in the deferred-fill list
+    uint32_t fill_work;                     // next fill row the fill kernel hands out
     uint32_t pad_;
 };
 
@@ -46,6 +48,7 @@ struct LevelPlan {
     uint32_t side[ASK_MAX_LEVELS];          // nominal region side at level i
     uint32_t split[ASK_MAX_LEVELS];         // 1 if non-uniform regions of level i split
     uint64_t max_regions[ASK_MAX_LEVELS];   // upper bound on regions at level i
+    uint32_t chunks[ASK_MAX_LEVELS];        // perimeter chunks per region (work items)
     uint32_t axis0;                         // non-empty initial regions per axis
 };
 
@@ -64,7 +67,7 @@ struct DeviceInfo {
 cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t max_dwell,
                               uint32_t bx, uint32_t by, bool count, DevCounters *ctr,
                               cudaStream_t s);
-cudaError_t launch_init(uint2 *olt0, DevCounters *ctr, uint32_t n, uint32_t s0,
+cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
                         uint32_t axis0, cudaStream_t s);
 
 struct LevelArgs {
@@ -79,15 +82,33 @@ struct LevelArgs {
     uint32_t r;
     const uint2 *olt_in;
     uint2 *olt_out;
-    uint32_t olt_cap;     // capacity of olt_out
+    uint32_t olt_cap;     // capacity of both region tables
+    uint32_t chunks;      // perimeter chunks per region at this level (1 = one warp per region)
+    uint32_t next_chunks; // chunks per region at the next level
+    uint4 *rst_in;        // per-region query state of this level (chunks > 1)
+    uint4 *rst_out;       // state of the next level's regions, set when they are appended
     uint2 *leaves;
     uint32_t leaf_cap;
+    uint4 *fills;         // deferred fills (region record, dwell); NULL = fill in place
+    uint32_t fill_cap;
     uint32_t exact_last;  // last level: evaluate whole perimeters and write them
     DevCounters *ctr;
 };
-// mode: 0 = one warp per region, 1 = one CTA of `threads` per region
-cudaError_t launch_level(const LevelArgs &a, int mode, uint32_t threads, bool count,
-                         int sms, cudaStream_t s);
+// Perimeter pixels per work item of a level kernel.
+constexpr uint32_t kChunkPx = 128;
+// Uniform regions larger than this are filled by the fill kernel.
+constexpr uint32_t kInPlaceFillArea = 16384;
+cudaError_t launch_level(const LevelArgs &a, bool count, int sms, cudaStream_t s);
+
+struct FillArgs {
+    uint32_t *map;
+    uint32_t n;
+    const uint4 *fills;
+    uint32_t fill_cap;
+    uint32_t max_rows;    // largest height of a deferred region
+    DevCounters *ctr;
+};
+cudaError_t launch_fill(const FillArgs &f, int sms, cudaStream_t s);
 
 struct LeafArgs {
     uint32_t *map;

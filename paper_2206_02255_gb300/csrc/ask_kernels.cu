@@ -1,5 +1,6 @@
 // ask_kernels.cu -- exhaustive kernel and the Adaptive Serial Kernels (ASK)
-// pipeline: init, one level kernel per subdivision depth, leaf kernel.
+// pipeline: init, one level kernel per subdivision depth, deferred fills,
+// leaf kernel.
 //
 // ASK (paper Sec. 5): the active regions of depth i sit in a device-resident
 // offset lookup table (read-OLT, Sec. 5.2).  One kernel per depth evaluates
@@ -12,15 +13,20 @@
 // terminal pass of Sec. 5.1, L(n, tau) of Sec. 4.2).
 //
 // GB300 layout of that scheme:
-//  * level kernels are persistent (a grid sized to the SM count) and read the
-//    region count from device memory, so no depth needs a host round trip
-//    and the whole sequence is a fixed chain of launches;
-//  * perimeter dwells are staged in shared memory; a uniform perimeter is
-//    detected with warp min/max reductions (__reduce_min/max_sync);
-//  * deep levels run one warp per region and compact their appends per warp:
-//    each lane keeps the outcome of one region the warp processed, then one
-//    atomicAdd per list reserves space for up to 32 regions at once (the
+//  * level kernels are persistent (a grid sized to the SM count), read the
+//    region count from device memory and hand out work with an atomic
+//    counter, so no depth needs a host round trip;
+//  * a work item is one region's perimeter, or one chunk of kChunkPx
+//    perimeter pixels of a large region (several warps per region: the MBR
+//    mapping of Sec. 4.3.2 applied to the query), one warp per item;
+//  * a query stops at the first two perimeter dwells known to differ; warps
+//    of one region share that verdict through a per-region state word, and
+//    the warp that finishes the region's last chunk takes the decision;
+//  * decisions are compacted per warp: each lane keeps the outcome of one
+//    region, then one atomicAdd per list serves up to 32 regions (the
 //    block-scan + single atomic alternative of Sec. 5.3.1, at warp scope);
+//  * large uniform regions are filled by a separate HBM-bound fill kernel
+//    with 128-bit stores over all SMs; small ones in place by their warp;
 //  * the OLTs are preallocated for the worst case, so nothing is resized
 //    between depths (Sec. 5.3.2 reallocates instead).
 #include <cuda_runtime.h>
@@ -35,10 +41,10 @@ namespace ask {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint32_t kWarpStage = 512;     // staged perimeter pixels per warp
-constexpr uint32_t kCtaStageMax = 16384; // staged perimeter pixels per CTA
+constexpr uint32_t kWarpStage = 512;  // staged perimeter pixels per warp (exact last level)
+constexpr uint32_t kNone = 0xffffffffu;
 
-enum : uint32_t { KIND_NONE = 0, KIND_FILL = 1, KIND_SPLIT = 2, KIND_LEAF = 3 };
+enum : uint32_t { KIND_NONE = 0, KIND_FILL = 1, KIND_SPLIT = 2, KIND_LEAF = 3, KIND_FILL_LATER = 4 };
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
@@ -74,10 +80,11 @@ __global__ void __launch_bounds__(1024) exhaustive_kernel(uint32_t *__restrict__
     }
 }
 
-// Zero the per-render counters (the latched error word is kept) and write
-// the level-0 OLT: the axis0 x axis0 non-empty initial regions of side s0.
-__global__ void init_kernel(uint2 *__restrict__ olt0, DevCounters *ctr, uint32_t n, uint32_t s0,
-                            uint32_t axis0)
+// Zero the per-render counters (the latched error word is kept), write the
+// level-0 OLT (the axis0 x axis0 non-empty initial regions of side s0) and,
+// when level 0 is queried in chunks, its per-region state.
+__global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, DevCounters *ctr,
+                            uint32_t n, uint32_t s0, uint32_t axis0)
 {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -96,23 +103,25 @@ __global__ void init_kernel(uint2 *__restrict__ olt0, DevCounters *ctr, uint32_t
         const uint32_t gx = k % axis0, gy = k / axis0;
         const uint32_t x0 = gx * s0, y0 = gy * s0;
         olt0[k] = pack_region(x0, y0, min(s0, n - x0), min(s0, n - y0));
+        if (rst0 != nullptr)
+            rst0[k] = make_uint4(kNone, 0u, 0u, 0u);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Level kernel, one warp per region.
+// Per-warp record of decided regions, flushed with one atomic per list.
 // ---------------------------------------------------------------------------
 struct WarpBatch {
-    uint2 rec;       // lane j: OLT record of the j-th region of the batch
+    uint2 rec;       // lane j: OLT record of the j-th region decided
     uint32_t kind;   // KIND_*
     uint32_t nchild; // children of a splitting region
+    uint32_t dwell;  // dwell of a uniform region filled later
 };
 
-// Reserve list space for the batch with one atomicAdd per list and write the
-// leaf records and child records.  Called by all 32 lanes.
 __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, uint32_t lane)
 {
     DevCounters *ctr = a.ctr;
+    const unsigned lt = (1u << lane) - 1u;
     // leaves: ballot + popc gives each leaf its slot
     const unsigned leaf_mask = __ballot_sync(kFull, b.kind == KIND_LEAF);
     if (leaf_mask) {
@@ -121,11 +130,26 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, ui
             base = atomicAdd(&ctr->leaf_count, (uint32_t)__popc(leaf_mask));
         base = __shfl_sync(kFull, base, 0);
         if (b.kind == KIND_LEAF) {
-            const uint32_t slot = base + (uint32_t)__popc(leaf_mask & ((1u << lane) - 1u));
+            const uint32_t slot = base + (uint32_t)__popc(leaf_mask & lt);
             if (slot < a.leaf_cap)
                 a.leaves[slot] = b.rec;
             else
                 atomicOr(&ctr->error, ERR_LEAF_OVERFLOW);
+        }
+    }
+    // large uniform regions for the fill kernel
+    const unsigned later_mask = __ballot_sync(kFull, b.kind == KIND_FILL_LATER);
+    if (later_mask) {
+        uint32_t base = 0;
+        if (lane == 0)
+            base = atomicAdd(&ctr->fill_count, (uint32_t)__popc(later_mask));
+        base = __shfl_sync(kFull, base, 0);
+        if (b.kind == KIND_FILL_LATER) {
+            const uint32_t slot = base + (uint32_t)__popc(later_mask & lt);
+            if (slot < a.fill_cap)
+                a.fills[slot] = make_uint4(b.rec.x, b.rec.y, b.dwell, 0u);
+            else
+                atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
         }
     }
     // children: warp inclusive scan of child counts, one atomicAdd
@@ -147,14 +171,17 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, ui
             const uint32_t first = base + incl - b.nchild;
             for (uint32_t j = 0; j < b.nchild; ++j) {
                 const uint32_t slot = first + j;
-                if (slot < a.olt_cap)
+                if (slot < a.olt_cap) {
                     a.olt_out[slot] = child_region(g, a.child_side, a.r, j);
-                else
+                    if (a.next_chunks > 1u)
+                        a.rst_out[slot] = make_uint4(kNone, 0u, 0u, 0u);
+                } else {
                     atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
+                }
             }
         }
     }
-    const unsigned fill_mask = __ballot_sync(kFull, b.kind == KIND_FILL);
+    const unsigned fill_mask = __ballot_sync(kFull, b.kind == KIND_FILL || b.kind == KIND_FILL_LATER);
     const unsigned split_mask = __ballot_sync(kFull, b.kind == KIND_SPLIT);
     if (lane == 0) {
         if (fill_mask)
@@ -166,96 +193,243 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, ui
     b.nchild = 0;
 }
 
+// Region state of a chunked query, read by lane 0 and broadcast.
+__device__ __forceinline__ uint2 read_state(const uint4 *st, uint32_t lane)
+{
+    uint2 v = make_uint2(kNone, 0u);
+    if (lane == 0) {
+        const volatile uint32_t *p = reinterpret_cast<const volatile uint32_t *>(st);
+        v.x = p[0];
+        v.y = p[1];
+    }
+    v.x = __shfl_sync(kFull, v.x, 0);
+    v.y = __shfl_sync(kFull, v.y, 0);
+    return v;
+}
+
+// One chunk [k0, k1) of a large region's perimeter, queried by one warp.  The
+// region's state st: x = common dwell found so far (kNone: none yet),
+// y = 1 once two dwells are known to differ, z = chunks finished.  Chunks of
+// the same region run on other warps at the same time and stop as soon as
+// one of them has set y.
+__device__ __forceinline__ void chunk_query(const LevelArgs &a, const Region &g, uint32_t k0,
+                                            uint32_t k1, uint4 *st, uint32_t lane,
+                                            unsigned long long &it)
+{
+    for (uint32_t base = k0; base < k1; base += 32u) {
+        if (read_state(st, lane).y)
+            return;
+        const uint32_t k = base + lane;
+        const bool active = k < k1;
+        const unsigned amask = __ballot_sync(kFull, active);
+        uint32_t px = g.x0, py = g.y0;
+        if (active)
+            perimeter_pixel(g, k, px, py);
+        Orbit o = orbit_start(pixel_c(a.pm, px, py));
+        bool done = !active, differ = false, stop = false;
+        for (;;) {
+            const uint2 v = read_state(st, lane);
+            if (v.y) {
+                stop = true;
+                break;
+            }
+            const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
+            if (!done)
+                done = orbit_round(o, limit);
+            const unsigned dm = __ballot_sync(kFull, done) & amask;
+            if (dm == amask)
+                break;
+            if (dm) {
+                differ = true;
+                break;
+            }
+        }
+        if (active)
+            it += o.d;
+        if (stop)
+            return;
+        if (differ) {
+            if (lane == 0)
+                atomicExch(&st->y, 1u);
+            return;
+        }
+        const uint32_t vmin = __reduce_min_sync(kFull, active ? o.d : kNone);
+        const uint32_t vmax = __reduce_max_sync(kFull, active ? o.d : 0u);
+        if (lane == 0) {
+            if (vmin != vmax) {
+                atomicExch(&st->y, 1u);
+            } else {
+                const uint32_t old = atomicCAS(&st->x, kNone, vmin);
+                if (old != kNone && old != vmin)
+                    atomicExch(&st->y, 1u);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// One chunk [k0, k1) of a large last-level region with exact perimeters:
+// every dwell is computed and written; st.x / st.y collect min / max.
+__device__ __forceinline__ void chunk_exact(const LevelArgs &a, const Region &g, uint32_t k0,
+                                            uint32_t k1, uint4 *st, uint32_t lane,
+                                            unsigned long long &it)
+{
+    uint32_t dmin = kNone, dmax = 0u;
+    for (uint32_t k = k0 + lane; k < k1; k += 32u) {
+        uint32_t px, py;
+        perimeter_pixel(g, k, px, py);
+        const float2 c = pixel_c(a.pm, px, py);
+        const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+        a.map[(size_t)py * a.n + px] = d;
+        dmin = min(dmin, d);
+        dmax = max(dmax, d);
+        it += d;
+    }
+    dmin = __reduce_min_sync(kFull, dmin);
+    dmax = __reduce_max_sync(kFull, dmax);
+    if (lane == 0) {
+        atomicMin(&st->x, dmin);
+        atomicMax(&st->y, dmax);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level kernel: one warp per work item (a region, or a perimeter chunk of a
+// large region).
+// ---------------------------------------------------------------------------
 template <bool COUNT>
-__global__ void __launch_bounds__(256) level_warp_kernel(LevelArgs a, uint32_t olt_in_cap)
+__global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
 {
     extern __shared__ uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *stage = smem + (threadIdx.x >> 5) * kWarpStage;
-    const uint32_t count = min(a.ctr->count[a.level], olt_in_cap);
+    const uint32_t count = min(a.ctr->count[a.level], a.olt_cap);
+    const uint32_t chunks = a.chunks;
+    const uint32_t items = count * chunks;  // the host keeps this below 2^32
+    const bool query = a.split || !a.exact_last;
 
     WarpBatch b;
     b.rec = make_uint2(0, 0);
     b.kind = KIND_NONE;
     b.nchild = 0;
+    b.dwell = 0;
     uint32_t j = 0;
     unsigned long long it = 0, bpx = 0, fpx = 0;
 
     for (;;) {
-        // regions are handed out one at a time: their costs differ by orders
+        // items are handed out one at a time: their costs differ by orders
         // of magnitude (a uniform perimeter inside the set runs to max_dwell)
-        uint32_t idx = 0;
+        uint32_t t = 0;
         if (lane == 0)
-            idx = atomicAdd(&a.ctr->work[a.level], 1u);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= count)
+            t = atomicAdd(&a.ctr->work[a.level], 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= items)
             break;
-        const uint2 e = a.olt_in[idx];
+        const uint32_t region = (chunks == 1u) ? t : t / chunks;
+        const uint2 e = a.olt_in[region];
         const Region g = unpack_region(e);
-        uint32_t kind;
-        if (a.split || !a.exact_last) {
-            // only "uniform, and to what" matters: stop at the first difference
-            // (a leaf's pixels, perimeter included, are then all computed by
-            // the leaf kernel)
-            uint32_t wv = 0;
-            if (warp_perimeter_uniform(a.pm, a.max_dwell, g, lane, &wv, it)) {
-                fill_rect(a.map, a.n, g, wv, lane, 32u);
-                kind = KIND_FILL;
+        const uint32_t P = perimeter_size(g.w, g.h);
+        bool decided = false, uniform = false;
+        uint32_t wv = 0;
+
+        if (chunks == 1u) {
+            decided = true;
+            if (COUNT && lane == 0)
+                bpx += P;
+            if (query) {
+                uniform = warp_perimeter_uniform(a.pm, a.max_dwell, g, lane, &wv, it);
+            } else {
+                // last level, exact perimeters staged in shared memory: a leaf
+                // keeps them and the leaf kernel skips them
+                uint32_t dmin = kNone, dmax = 0u;
+                for (uint32_t k = lane; k < P; k += 32u) {
+                    uint32_t px, py;
+                    perimeter_pixel(g, k, px, py);
+                    const float2 c = pixel_c(a.pm, px, py);
+                    const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+                    dmin = min(dmin, d);
+                    dmax = max(dmax, d);
+                    if (k < kWarpStage)
+                        stage[k] = d;
+                    else
+                        a.map[(size_t)py * a.n + px] = d;  // beyond the stage: write through
+                    if (COUNT)
+                        it += d;
+                }
+                dmin = __reduce_min_sync(kFull, dmin);
+                dmax = __reduce_max_sync(kFull, dmax);
+                uniform = (dmin == dmax);
+                wv = dmin;
+                if (!uniform) {
+                    const uint32_t staged = min(P, kWarpStage);
+                    for (uint32_t k = lane; k < staged; k += 32u) {
+                        uint32_t px, py;
+                        perimeter_pixel(g, k, px, py);
+                        a.map[(size_t)py * a.n + px] = stage[k];
+                    }
+                }
+            }
+        } else {
+            const uint32_t c = t - region * chunks;
+            uint4 *st = a.rst_in + region;
+            const uint32_t k0 = min(P, c * kChunkPx), k1 = min(P, k0 + kChunkPx);
+            if (COUNT && lane == 0)
+                bpx += k1 - k0;
+            if (k0 < k1) {
+                if (query)
+                    chunk_query(a, g, k0, k1, st, lane, it);
+                else
+                    chunk_exact(a, g, k0, k1, st, lane, it);
+            }
+            // the warp that finishes the region's last chunk decides
+            uint32_t last = 0;
+            if (lane == 0) {
+                __threadfence();
+                last = (atomicAdd(&st->z, 1u) == chunks - 1u) ? 1u : 0u;
+                if (last)
+                    __threadfence();
+            }
+            last = __shfl_sync(kFull, last, 0);
+            if (last) {
+                uint32_t sx = 0, sy = 0;
+                if (lane == 0) {
+                    sx = atomicAdd(&st->x, 0u);
+                    sy = atomicAdd(&st->y, 0u);
+                }
+                sx = __shfl_sync(kFull, sx, 0);
+                sy = __shfl_sync(kFull, sy, 0);
+                uniform = query ? (sy == 0u && sx != kNone) : (sx == sy);
+                wv = sx;
+                decided = true;
+            }
+        }
+
+        if (decided) {
+            uint32_t kind;
+            if (uniform) {
+                const uint32_t area = g.w * g.h;
+                if (a.fills != nullptr && area > kInPlaceFillArea) {
+                    kind = KIND_FILL_LATER;
+                } else {
+                    fill_rect(a.map, a.n, g, wv, lane, 32u);
+                    kind = KIND_FILL;
+                }
                 if (COUNT && lane == 0)
-                    fpx += (unsigned long long)g.w * g.h;
+                    fpx += area;
             } else {
                 kind = a.split ? KIND_SPLIT : KIND_LEAF;
             }
-            if (COUNT && lane == 0)
-                bpx += perimeter_size(g.w, g.h);
-        } else {
-            // last level, exact perimeters: every perimeter dwell is final (a
-            // leaf keeps them and the leaf kernel skips them)
-            const uint32_t P = perimeter_size(g.w, g.h);
-            uint32_t dmin = 0xffffffffu, dmax = 0u;
-            for (uint32_t k = lane; k < P; k += 32u) {
-                uint32_t px, py;
-                perimeter_pixel(g, k, px, py);
-                const float2 c = pixel_c(a.pm, px, py);
-                const uint32_t d = dwell(c.x, c.y, a.max_dwell);
-                dmin = min(dmin, d);
-                dmax = max(dmax, d);
-                if (k < kWarpStage)
-                    stage[k] = d;
-                else
-                    a.map[(size_t)py * a.n + px] = d;  // beyond the stage: write through
-                if (COUNT) {
-                    it += d;
-                    ++bpx;
-                }
+            if (lane == j) {
+                b.rec = e;
+                b.kind = kind;
+                b.dwell = wv;
+                b.nchild = (kind == KIND_SPLIT) ? child_count(g, a.child_side, a.r) : 0u;
             }
-            dmin = __reduce_min_sync(kFull, dmin);
-            dmax = __reduce_max_sync(kFull, dmax);
-            if (dmin == dmax) {
-                fill_rect(a.map, a.n, g, dmin, lane, 32u);
-                kind = KIND_FILL;
-                if (COUNT && lane == 0)
-                    fpx += (unsigned long long)g.w * g.h;
-            } else {
-                // leaf: its perimeter is final, the leaf kernel skips it
-                const uint32_t staged = min(P, kWarpStage);
-                for (uint32_t k = lane; k < staged; k += 32u) {
-                    uint32_t px, py;
-                    perimeter_pixel(g, k, px, py);
-                    a.map[(size_t)py * a.n + px] = stage[k];
-                }
-                kind = KIND_LEAF;
+            __syncwarp();
+            if (++j == 32u) {
+                flush_batch(a, b, lane);
+                j = 0;
             }
-        }
-        if (lane == j) {
-            b.rec = e;
-            b.kind = kind;
-            b.nchild = (kind == KIND_SPLIT) ? child_count(g, a.child_side, a.r) : 0u;
-        }
-        __syncwarp();
-        if (++j == 32u) {
-            flush_batch(a, b, lane);
-            j = 0;
         }
     }
     if (j)
@@ -278,146 +452,35 @@ __global__ void __launch_bounds__(256) level_warp_kernel(LevelArgs a, uint32_t o
 }
 
 // ---------------------------------------------------------------------------
-// Level kernel, one CTA per region (large regions, few of them).
+// Fill kernel: the large uniform regions, one row per warp item, 128-bit
+// stores; pure HBM writes spread over every SM.
 // ---------------------------------------------------------------------------
-template <bool COUNT>
-__global__ void __launch_bounds__(1024) level_cta_kernel(LevelArgs a, uint32_t olt_in_cap,
-                                                         uint32_t stage_cap)
+__global__ void __launch_bounds__(256) fill_kernel(FillArgs f)
 {
-    extern __shared__ uint32_t stage[];
-    __shared__ uint32_t red_min[32], red_max[32];
-    __shared__ uint32_t s_min, s_max, s_base, s_flag, s_w, s_idx;
-    const uint32_t tid = threadIdx.x, T = blockDim.x, lane = tid & 31u, wid = tid >> 5;
-    const uint32_t nw = T >> 5;
-    const uint32_t count = min(a.ctr->count[a.level], olt_in_cap);
-    unsigned long long it = 0, bpx = 0, fpx = 0;
-    const bool query = a.split || !a.exact_last;
-
-    for (;;) {
-        if (tid == 0)
-            s_idx = atomicAdd(&a.ctr->work[a.level], 1u);
-        __syncthreads();
-        const uint32_t idx = s_idx;
-        if (idx >= count)
-            break;  // uniform over the CTA
-        const uint2 e = a.olt_in[idx];
-        const Region g = unpack_region(e);
-        const uint32_t P = perimeter_size(g.w, g.h);
-        uint32_t dmin, dmax;
-        if (query) {
-            if (tid == 0) {
-                s_flag = 0u;
-                s_w = 0xffffffffu;
-            }
-            __syncthreads();
-            uint32_t wv = 0;
-            const bool uni = cta_perimeter_uniform(a.pm, a.max_dwell, g, tid, T, &s_flag, &s_w, &wv, it);
-            dmin = wv;
-            dmax = uni ? wv : wv + 1u;
-            if (COUNT && tid == 0)
-                bpx += P;
-        } else {
-            dmin = 0xffffffffu;
-            dmax = 0u;
-            for (uint32_t k = tid; k < P; k += T) {
-                uint32_t px, py;
-                perimeter_pixel(g, k, px, py);
-                const float2 c = pixel_c(a.pm, px, py);
-                const uint32_t d = dwell(c.x, c.y, a.max_dwell);
-                dmin = min(dmin, d);
-                dmax = max(dmax, d);
-                if (k < stage_cap)
-                    stage[k] = d;
-                else
-                    a.map[(size_t)py * a.n + px] = d;
-                if (COUNT) {
-                    it += d;
-                    ++bpx;
-                }
-            }
-            dmin = __reduce_min_sync(kFull, dmin);
-            dmax = __reduce_max_sync(kFull, dmax);
-            if (lane == 0) {
-                red_min[wid] = dmin;
-                red_max[wid] = dmax;
-            }
-            __syncthreads();
-            if (wid == 0) {
-                uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
-                uint32_t m1 = lane < nw ? red_max[lane] : 0u;
-                m0 = __reduce_min_sync(kFull, m0);
-                m1 = __reduce_max_sync(kFull, m1);
-                if (lane == 0) {
-                    s_min = m0;
-                    s_max = m1;
-                }
-            }
-            __syncthreads();
-            dmin = s_min;
-            dmax = s_max;
-        }
-        if (dmin == dmax) {
-            fill_rect(a.map, a.n, g, dmin, tid, T);
-            if (tid == 0) {
-                atomicAdd(&a.ctr->fills[a.level], 1u);
-                if (COUNT)
-                    fpx += (unsigned long long)g.w * g.h;
-            }
-        } else if (a.split) {
-            const uint32_t nc = child_count(g, a.child_side, a.r);
-            if (tid == 0) {
-                s_base = atomicAdd(&a.ctr->count[a.level + 1], nc);
-                atomicAdd(&a.ctr->subdivs[a.level], 1u);
-            }
-            __syncthreads();
-            for (uint32_t j = tid; j < nc; j += T) {
-                const uint32_t slot = s_base + j;
-                if (slot < a.olt_cap)
-                    a.olt_out[slot] = child_region(g, a.child_side, a.r, j);
-                else
-                    atomicOr(&a.ctr->error, ERR_OLT_OVERFLOW);
-            }
-        } else {
-            if (!query) {
-                const uint32_t staged = min(P, stage_cap);
-                for (uint32_t k = tid; k < staged; k += T) {
-                    uint32_t px, py;
-                    perimeter_pixel(g, k, px, py);
-                    a.map[(size_t)py * a.n + px] = stage[k];
-                }
-            }
-            if (tid == 0) {
-                const uint32_t slot = atomicAdd(&a.ctr->leaf_count, 1u);
-                if (slot < a.leaf_cap)
-                    a.leaves[slot] = e;
-                else
-                    atomicOr(&a.ctr->error, ERR_LEAF_OVERFLOW);
-            }
-        }
-        __syncthreads();  // the stage and s_* are reused by the next region
-    }
-    __syncthreads();
-    if (COUNT) {
-        it = warp_sum_u64(it);
-        bpx = warp_sum_u64(bpx);
-        fpx = warp_sum_u64(fpx);
-        if (lane == 0) {
-            if (it) {
-                atomicAdd(&a.ctr->iterations, it);
-                atomicAdd(&a.ctr->level_iters[a.level], it);
-            }
-            if (bpx)
-                atomicAdd(&a.ctr->border_pixels, bpx);
-            if (fpx)
-                atomicAdd(&a.ctr->fill_pixels, fpx);
-        }
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nfill = min(f.ctr->fill_count, f.fill_cap);
+    const uint32_t rows = f.max_rows;
+    const unsigned long long total = (unsigned long long)nfill * rows;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long item = warp; item < total; item += nwarps) {
+        const uint32_t fi = (uint32_t)(item / rows);
+        const uint32_t row = (uint32_t)(item - (unsigned long long)fi * rows);
+        const uint4 e = f.fills[fi];
+        const Region g = unpack_region(make_uint2(e.x, e.y));
+        if (row >= g.h)
+            continue;
+        Region r1 = g;
+        r1.y0 = g.y0 + row;
+        r1.h = 1;
+        fill_rect(f.map, f.n, r1, e.z, lane, 32u);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Leaf kernel: every interior pixel of every leaf region.  Work items are
-// (leaf, tile) pairs with block_x x block_y tiles; the grid is persistent and
-// each warp walks the item sequence on its own (no CTA barrier).
+// Tiled leaf kernel (ASK_FLAG_LEAF_TILED): (leaf, tile) items with block_x x
+// block_y tiles, one thread per pixel; persistent grid, warps walk the item
+// sequence on their own.
 // ---------------------------------------------------------------------------
 template <bool COUNT>
 __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_cap, uint32_t tiles_x,
@@ -458,35 +521,58 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 }
 
 // ---------------------------------------------------------------------------
-// Leaf kernel with lane refill.  Leaf pixels near the set's boundary have
-// dwells from a handful of updates to max_dwell side by side, so a warp that
-// owned 32 fixed pixels would idle most lanes while one orbit runs on.  Here
-// each warp takes leaves from a device counter and feeds their pixels to its
-// lanes one at a time:
+// Leaf kernel with lane refill (default).  Leaf pixels near the set's
+// boundary have dwells from a handful of updates to max_dwell side by side,
+// so a warp that owned 32 fixed pixels would idle most lanes while one orbit
+// runs on.  Here each warp takes leaves from a device counter and feeds their
+// pixels to its lanes one at a time:
 //  * every round, each busy lane advances its orbit by one unchecked block
 //    (see dwell()); a lane whose block ends escaped, or that has fewer than a
 //    block's worth of updates left, parks (saved state, count, pixel) in the
-//    warp's replay buffer in shared memory and takes a new pixel at once;
-//  * when 32 orbits are parked, the warp replays them together, one per
-//    lane, with a tested update per step (at most one block each), and
-//    writes their dwells.
-// Lanes stay busy until the warp runs out of leaves.
+//    warp's buffer in shared memory and takes a new pixel at once;
+//  * when 32 orbits are parked, the warp finishes them together, one per
+//    lane: a binary search over the parked block (unchecked half blocks and
+//    one test each, the same number of steps on every lane) finds the exact
+//    escape, and the dwells are written.
 // ---------------------------------------------------------------------------
 constexpr int kRefillWarps = 8;   // warps per CTA
 constexpr uint32_t kParkCap = 64; // parked orbits per warp (< 32 + 32)
 
+// Exact dwell of a parked orbit: state (x, y) after d updates, that state
+// known to pass the test, and "escaped, or d >= max_dwell" known to hold
+// kUnroll updates later.  Points where escape is not absorbing take the
+// tested loop instead.
 template <bool COUNT>
-__device__ __forceinline__ void replay_parked(const LeafArgs &a, float4 f, uint2 u,
+__device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2 u,
                                               unsigned long long &it)
 {
-    float x = f.x, y = f.y;
-    const float cr = f.z, ci = f.w;
-    uint32_t d = u.x;
-    while (d < a.max_dwell && z_bounded(x, y)) {
-        z_update(x, y, cr, ci);
-        ++d;
-    }
     const uint32_t px = u.y & 0xffffu, py = u.y >> 16;
+    const float2 c = pixel_c(a.pm, px, py);
+    uint32_t d = u.x;
+    float x = s.x, y = s.y;
+    if (!escape_absorbing(c.x, c.y)) {
+        while (d < a.max_dwell && z_bounded(x, y)) {
+            z_update(x, y, c.x, c.y);
+            ++d;
+        }
+    } else if (d < a.max_dwell) {
+        // invariant: count d passes (d < max_dwell) and the predicate holds
+        // at d + 2h; halve h until the first count where it holds is d + 1
+#pragma unroll
+        for (uint32_t h = (uint32_t)kUnroll / 2u; h >= 1u; h >>= 1) {
+            float tx = x, ty = y;
+#pragma unroll
+            for (uint32_t k = 0; k < h; ++k)
+                z_update(tx, ty, c.x, c.y);
+            const bool hit = (a.max_dwell - d <= h) || !z_bounded(tx, ty);
+            if (!hit) {
+                x = tx;
+                y = ty;
+                d += h;
+            }
+        }
+        d += 1u;
+    }
     a.map[(size_t)py * a.n + px] = d;
     if (COUNT)
         it += d;
@@ -495,20 +581,17 @@ __device__ __forceinline__ void replay_parked(const LeafArgs &a, float4 f, uint2
 template <bool COUNT>
 __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs a)
 {
-    __shared__ float4 park_f[kRefillWarps][kParkCap];  // saved x, y and c
+    __shared__ float2 park_s[kRefillWarps][kParkCap];  // saved state
     __shared__ uint2 park_u[kRefillWarps][kParkCap];   // count, pixel (py << 16 | px)
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    float4 *qf = park_f[wib];
+    float2 *qs = park_s[wib];
     uint2 *qu = park_u[wib];
     uint32_t parked = 0;  // warp-uniform
 
     const uint32_t nleaves = min(a.ctr->leaf_count, a.leaf_cap);
     const uint32_t K = (uint32_t)kUnroll;
     // the warp's current leaf: the part still to hand out, as a row-major cursor
-    Region g;
-    g.x0 = g.y0 = 0;
-    g.w = g.h = 1;
     uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1;
     bool more = true;
     // this lane's orbit
@@ -530,11 +613,11 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                     more = false;
                     break;
                 }
-                g = unpack_region(a.leaves[li]);
+                const Region g = unpack_region(a.leaves[li]);
                 if (a.skip_perimeter) {
                     // only the interior; a leaf of side <= 2 is all perimeter
-                    cw = g.w > 2u ? g.w - 2u : 0u;
-                    rem = (g.w > 2u && g.h > 2u) ? cw * (g.h - 2u) : 0u;
+                    cw = g.w > 2u ? g.w - 2u : 1u;
+                    rem = (g.w > 2u && g.h > 2u) ? (g.w - 2u) * (g.h - 2u) : 0u;
                     ox = g.x0 + 1u;
                     oy = g.y0 + 1u;
                 } else {
@@ -546,8 +629,7 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                 row0 = col0 = 0;
                 continue;
             }
-            const uint32_t nidle = (uint32_t)__popc(idle);
-            const uint32_t take = min(nidle, rem);
+            const uint32_t take = min((uint32_t)__popc(idle), rem);
             const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
             if (!busy && rank < take) {
                 uint32_t col = col0 + rank, row = row0;
@@ -579,50 +661,50 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
 
         // ---- one unchecked block per busy lane
         bool park = false;
-        float sx = x, sy = y;
+        const float sx = x, sy = y;
         if (busy) {
             if (fast && a.max_dwell - d >= K) {
 #pragma unroll
                 for (int k = 0; k < kUnroll; ++k)
                     z_update(x, y, cr, ci);
-                if (z_bounded(x, y)) {
+                if (z_bounded(x, y))
                     d += K;
-                } else {
-                    park = true;  // escaped inside this block: replay it
-                }
+                else
+                    park = true;  // escaped inside this block
             } else {
                 park = true;      // tail below max_dwell, or |c| near 2
             }
         }
 
-        // ---- park finished orbits; replay 32 at a time
+        // ---- park finished orbits; finish 32 at a time
         const unsigned pmask = __ballot_sync(kFull, park);
         if (pmask) {
             if (park) {
                 const uint32_t slot = parked + (uint32_t)__popc(pmask & lt_mask);
-                qf[slot] = make_float4(sx, sy, cr, ci);
+                qs[slot] = make_float2(sx, sy);
                 qu[slot] = make_uint2(d, pix);
                 busy = false;
             }
             parked += (uint32_t)__popc(pmask);
             __syncwarp();
             if (parked >= 32u) {
-                const float4 f = qf[lane];
+                const float2 s = qs[lane];
                 const uint2 u = qu[lane];
-                float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool mv = lane < parked - 32u;
+                float2 s2 = make_float2(0.f, 0.f);
                 uint2 u2 = make_uint2(0u, 0u);
-                if (lane < parked - 32u) {
-                    f2 = qf[32u + lane];
+                if (mv) {
+                    s2 = qs[32u + lane];
                     u2 = qu[32u + lane];
                 }
                 __syncwarp();
-                if (lane < parked - 32u) {
-                    qf[lane] = f2;
+                if (mv) {
+                    qs[lane] = s2;
                     qu[lane] = u2;
                 }
                 parked -= 32u;
                 __syncwarp();
-                replay_parked<COUNT>(a, f, u, it);
+                finish_parked<COUNT>(a, s, u, it);
                 if (COUNT)
                     ++lpx;
             }
@@ -630,7 +712,7 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
     }
     // ---- the orbits still parked
     if (lane < parked) {
-        replay_parked<COUNT>(a, qf[lane], qu[lane], it);
+        finish_parked<COUNT>(a, qs[lane], qu[lane], it);
         if (COUNT)
             ++lpx;
     }
@@ -676,8 +758,8 @@ cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t m
     return cudaGetLastError();
 }
 
-cudaError_t launch_init(uint2 *olt0, DevCounters *ctr, uint32_t n, uint32_t s0, uint32_t axis0,
-                        cudaStream_t s)
+cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
+                        uint32_t axis0, cudaStream_t s)
 {
     const uint32_t total = axis0 * axis0;
     uint32_t blocks = (total + 255u) / 256u;
@@ -685,43 +767,27 @@ cudaError_t launch_init(uint2 *olt0, DevCounters *ctr, uint32_t n, uint32_t s0, 
         blocks = 1;
     if (blocks > 4096)
         blocks = 4096;
-    init_kernel<<<blocks, 256, 0, s>>>(olt0, ctr, n, s0, axis0);
+    init_kernel<<<blocks, 256, 0, s>>>(olt0, rst0, ctr, n, s0, axis0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_level(const LevelArgs &a, int mode, uint32_t threads, bool count, int sms,
-                         cudaStream_t s)
+cudaError_t launch_level(const LevelArgs &a, bool count, int sms, cudaStream_t s)
 {
-    // both tables have the same capacity; a count past it (an overflow that
-    // the previous level latched) is clamped so nothing reads out of bounds
-    const uint32_t in_cap = a.olt_cap;
-    if (mode == 0) {
-        const size_t smem = (size_t)(256 / 32) * kWarpStage * sizeof(uint32_t);
-        if (count) {
-            const int grid = persistent_grid(level_warp_kernel<true>, 256, smem, sms);
-            level_warp_kernel<true><<<grid, 256, smem, s>>>(a, in_cap);
-        } else {
-            const int grid = persistent_grid(level_warp_kernel<false>, 256, smem, sms);
-            level_warp_kernel<false><<<grid, 256, smem, s>>>(a, in_cap);
-        }
+    const size_t smem = (size_t)(256 / 32) * kWarpStage * sizeof(uint32_t);
+    if (count) {
+        const int grid = persistent_grid(level_kernel<true>, 256, smem, sms);
+        level_kernel<true><<<grid, 256, smem, s>>>(a);
     } else {
-        const uint32_t P = 4u * a.side;
-        const uint32_t stage_cap = P < kCtaStageMax ? P : kCtaStageMax;
-        const size_t smem = (size_t)stage_cap * sizeof(uint32_t);
-        if (smem > 48 * 1024) {
-            cudaFuncSetAttribute(level_cta_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kCtaStageMax * sizeof(uint32_t)));
-            cudaFuncSetAttribute(level_cta_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kCtaStageMax * sizeof(uint32_t)));
-        }
-        if (count) {
-            const int grid = persistent_grid(level_cta_kernel<true>, (int)threads, smem, sms);
-            level_cta_kernel<true><<<grid, threads, smem, s>>>(a, in_cap, stage_cap);
-        } else {
-            const int grid = persistent_grid(level_cta_kernel<false>, (int)threads, smem, sms);
-            level_cta_kernel<false><<<grid, threads, smem, s>>>(a, in_cap, stage_cap);
-        }
+        const int grid = persistent_grid(level_kernel<false>, 256, smem, sms);
+        level_kernel<false><<<grid, 256, smem, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const FillArgs &f, int sms, cudaStream_t s)
+{
+    const int grid = persistent_grid(fill_kernel, 256, 0, sms);
+    fill_kernel<<<grid, 256, 0, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -200,7 +200,7 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
     // error word here; the init kernel zeroes the rest and writes OLT 0
     if (cudaMemsetAsync(&sc->ctr->error, 0, sizeof(uint32_t), s) != cudaSuccess)
         return ASK_ECUDA;
-    if (launch_init(sc->olt[0], sc->ctr, n, plan.side[0], plan.axis0, s) != cudaSuccess)
+    if (launch_init(sc->olt[0], nullptr, sc->ctr, n, plan.side[0], plan.axis0, s) != cudaSuccess)
         return ASK_ECUDA;
     const uint32_t L = plan.levels;
     for (uint32_t i = 0; i < L; ++i) {
@@ -217,14 +217,19 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
         a.olt_in = sc->olt[i & 1];
         a.olt_out = sc->olt[(i + 1) & 1];
         a.olt_cap = kNoAllocRegions;
+        // one warp per region and fills in place: no per-region query state
+        // or fill list, so the fixed scratch stays at three tables
+        a.chunks = 1u;
+        a.next_chunks = 1u;
+        a.rst_in = nullptr;
+        a.rst_out = nullptr;
         a.leaves = sc->leaves;
         a.leaf_cap = kNoAllocRegions;
+        a.fills = nullptr;
+        a.fill_cap = 0u;
         a.exact_last = 0u;
         a.ctr = sc->ctr;
-        const uint64_t warp_slots = (uint64_t)sc->sms * 16u;
-        const int mode = (plan.max_regions[i] < warp_slots && plan.side[i] >= 64u) ? 1 : 0;
-        const uint32_t threads = plan.side[i] >= 1024u ? 512u : 256u;
-        if (launch_level(a, mode, threads, false, sc->sms, s) != cudaSuccess)
+        if (launch_level(a, false, sc->sms, s) != cudaSuccess)
             return ASK_ECUDA;
     }
     LeafArgs la;
