@@ -285,14 +285,27 @@ def run_gpu(args):
     ms_step = max_over_ranks(world, ms_step, dev)
     timing = ctx.timing_read()
 
-    # ---- comparison arms at the same configuration (untimed for the headline)
+    # ---- comparison arms, each tuned on its own (untimed for the headline)
     ms_ex = ms_cdp = ms_cdp_fnf = float("nan")
+    ex_block = cdp_cfg = None
     if not args.no_compare:
         reps = max(3, args.steps // 4)
-        ms_ex = time_renders("exhaustive", g, r, B, blk, reps)
-        ms_cdp = time_renders("cdp2", g, r, B, blk, 2)
-        ms_cdp_fnf = time_renders("cdp2", g, r, B, blk, reps, ask.FLAG_CDP2_FIRE_AND_FORGET)
-
+        for blkx in inputs.BLOCK_SHAPES:
+            t = time_renders("exhaustive", g, r, B, blkx, 2)
+            if ex_block is None or t < ex_block[1]:
+                ex_block = (blkx, t)
+        ms_ex = time_renders("exhaustive", g, r, B, ex_block[0], reps)
+        fnf = ask.FLAG_CDP2_FIRE_AND_FORGET
+        for cg in (8, 16, 32, 64):
+            for cr in (2, 4):
+                for cB in (16, 32, 64, 128):
+                    for cblk in ((16, 16), (64, 8)):
+                        t = time_renders("cdp2", cg, cr, cB, cblk, 1, fnf)
+                        if cdp_cfg is None or t < cdp_cfg[4]:
+                            cdp_cfg = (cg, cr, cB, cblk, t)
+        cg, cr, cB, cblk = cdp_cfg[:4]
+        ms_cdp_fnf = time_renders("cdp2", cg, cr, cB, cblk, reps, fnf)
+        ms_cdp = time_renders("cdp2", cg, cr, cB, cblk, 1)
     pixels = float(n) * n
     value = world * pixels / (ms_step / 1e3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -357,9 +370,12 @@ def run_gpu(args):
             "dwell_iter_s": {"executed": cst["iterations"] / (ms_step / 1e3),
                              "exhaustive_equivalent": est["iterations"] / (ms_step / 1e3)},
             "exhaustive": {"ms": ms_ex, "gpix_s": pixels / (ms_ex / 1e3) / 1e9,
-                           "dwell_iter_s": est["iterations"] / (ms_ex / 1e3)},
+                           "dwell_iter_s": est["iterations"] / (ms_ex / 1e3),
+                           "block": list(ex_block[0]) if ex_block else None},
             "cdp2": {"ms_tail_launch": ms_cdp, "ms_fire_and_forget": ms_cdp_fnf,
-                     "gpix_s": pixels / (min(ms_cdp, ms_cdp_fnf) / 1e3) / 1e9},
+                     "gpix_s": pixels / (min(ms_cdp, ms_cdp_fnf) / 1e3) / 1e9,
+                     "tuned": ({"g": cdp_cfg[0], "r": cdp_cfg[1], "B": cdp_cfg[2],
+                                "block": list(cdp_cfg[3])} if cdp_cfg else None)},
             "speedup_vs_exhaustive": ms_ex / ms_step,
             "speedup_vs_cdp2": min(ms_cdp, ms_cdp_fnf) / ms_step,
             "mismatch_vs_exhaustive_pixels": mismatch,

@@ -227,11 +227,16 @@ __device__ __forceinline__ void chunk_query(const LevelArgs &a, const Region &g,
             perimeter_pixel(g, k, px, py);
         Orbit o = orbit_start(pixel_c(a.pm, px, py));
         bool done = !active, differ = false, stop = false;
+        uint2 v = read_state(st, lane);
+        const volatile uint32_t *ps = reinterpret_cast<const volatile uint32_t *>(st);
         for (;;) {
-            const uint2 v = read_state(st, lane);
-            if (v.y) {
-                stop = true;
-                break;
+            // the next state load is issued now and consumed after the block,
+            // so its L2 latency hides behind the updates; a stale value is
+            // harmless (the common dwell is set once, the flag only rises)
+            uint32_t nx = 0, ny = 0;
+            if (lane == 0) {
+                nx = ps[0];
+                ny = ps[1];
             }
             const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
             if (!done)
@@ -241,6 +246,12 @@ __device__ __forceinline__ void chunk_query(const LevelArgs &a, const Region &g,
                 break;
             if (dm) {
                 differ = true;
+                break;
+            }
+            v.x = __shfl_sync(kFull, nx, 0);
+            v.y = __shfl_sync(kFull, ny, 0);
+            if (v.y) {
+                stop = true;
                 break;
             }
         }
@@ -457,23 +468,25 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) fill_kernel(FillArgs f)
 {
+    constexpr uint32_t kBand = 8;  // rows per work item
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nfill = min(f.ctr->fill_count, f.fill_cap);
-    const uint32_t rows = f.max_rows;
-    const unsigned long long total = (unsigned long long)nfill * rows;
+    const uint32_t bands = (f.max_rows + kBand - 1u) / kBand;
+    const unsigned long long total = (unsigned long long)nfill * bands;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (unsigned long long item = warp; item < total; item += nwarps) {
-        const uint32_t fi = (uint32_t)(item / rows);
-        const uint32_t row = (uint32_t)(item - (unsigned long long)fi * rows);
+        const uint32_t fi = (uint32_t)(item / bands);
+        const uint32_t band = (uint32_t)(item - (unsigned long long)fi * bands);
         const uint4 e = f.fills[fi];
         const Region g = unpack_region(make_uint2(e.x, e.y));
+        const uint32_t row = band * kBand;
         if (row >= g.h)
             continue;
-        Region r1 = g;
-        r1.y0 = g.y0 + row;
-        r1.h = 1;
-        fill_rect(f.map, f.n, r1, e.z, lane, 32u);
+        Region rb = g;
+        rb.y0 = g.y0 + row;
+        rb.h = min(kBand, g.h - row);
+        fill_rect(f.map, f.n, rb, e.z, lane, 32u);
     }
 }
 
@@ -535,8 +548,8 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 //    one test each, the same number of steps on every lane) finds the exact
 //    escape, and the dwells are written.
 // ---------------------------------------------------------------------------
-constexpr int kRefillWarps = 8;   // warps per CTA
-constexpr uint32_t kParkCap = 64; // parked orbits per warp (< 32 + 32)
+constexpr int kRefillWarps = 8;    // warps per CTA
+constexpr uint32_t kParkCap = 128; // parked orbits per warp (< 32 + 2 * 32)
 
 // Exact dwell of a parked orbit: state (x, y) after d updates, that state
 // known to pass the test, and "escaped, or d >= max_dwell" known to hold
@@ -578,6 +591,29 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2
         it += d;
 }
 
+// One orbit slot of a lane.
+struct Slot {
+    float x, y, cr, ci;
+    uint32_t d, pix;
+    bool busy, fast;
+};
+
+__device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t px, uint32_t py)
+{
+    const float2 c = pixel_c(pm, px, py);
+    o.cr = c.x;
+    o.ci = c.y;
+    o.x = 0.0f;
+    o.y = 0.0f;
+    o.d = 0;
+    o.pix = (py << 16) | px;
+    o.fast = escape_absorbing(c.x, c.y);
+    o.busy = true;
+}
+
+// Each lane carries two independent orbits, so one round's bookkeeping
+// (votes, refills, parking) serves two blocks of updates, and the two update
+// chains interleave.
 template <bool COUNT>
 __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs a)
 {
@@ -594,16 +630,17 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
     // the warp's current leaf: the part still to hand out, as a row-major cursor
     uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1;
     bool more = true;
-    // this lane's orbit
-    bool busy = false, fast = false;
-    float x = 0.0f, y = 0.0f, cr = 0.0f, ci = 0.0f;
-    uint32_t d = 0, pix = 0;
+    Slot s0, s1;
+    s0.busy = s1.busy = false;
+    s0.fast = s1.fast = false;
+    s0.x = s0.y = s0.cr = s0.ci = s1.x = s1.y = s1.cr = s1.ci = 0.0f;
+    s0.d = s1.d = s0.pix = s1.pix = 0;
     unsigned long long it = 0, lpx = 0;
 
     for (;;) {
-        // ---- refill idle lanes
-        unsigned idle = __ballot_sync(kFull, !busy);
-        while (idle && more) {
+        // ---- refill idle slots: slot 0 of the idle lanes, then slot 1
+        unsigned i0 = __ballot_sync(kFull, !s0.busy), i1 = __ballot_sync(kFull, !s1.busy);
+        while ((i0 | i1) && more) {
             if (rem == 0) {
                 uint32_t li = 0;
                 if (lane == 0)
@@ -629,24 +666,25 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                 row0 = col0 = 0;
                 continue;
             }
-            const uint32_t take = min((uint32_t)__popc(idle), rem);
-            const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
-            if (!busy && rank < take) {
-                uint32_t col = col0 + rank, row = row0;
+            const uint32_t n0 = (uint32_t)__popc(i0);
+            const uint32_t take = min(n0 + (uint32_t)__popc(i1), rem);
+            const uint32_t r0 = (uint32_t)__popc(i0 & lt_mask);
+            const uint32_t r1 = n0 + (uint32_t)__popc(i1 & lt_mask);
+            if (!s0.busy && r0 < take) {
+                uint32_t col = col0 + r0, row = row0;
                 while (col >= cw) {
                     col -= cw;
                     ++row;
                 }
-                const uint32_t px = ox + col, py = oy + row;
-                const float2 c = pixel_c(a.pm, px, py);
-                cr = c.x;
-                ci = c.y;
-                x = 0.0f;
-                y = 0.0f;
-                d = 0;
-                pix = (py << 16) | px;
-                fast = escape_absorbing(cr, ci);
-                busy = true;
+                slot_start(s0, a.pm, ox + col, oy + row);
+            }
+            if (!s1.busy && r1 < take) {
+                uint32_t col = col0 + r1, row = row0;
+                while (col >= cw) {
+                    col -= cw;
+                    ++row;
+                }
+                slot_start(s1, a.pm, ox + col, oy + row);
             }
             col0 += take;
             while (col0 >= cw) {
@@ -654,57 +692,59 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                 ++row0;
             }
             rem -= take;
-            idle = __ballot_sync(kFull, !busy);
+            i0 = __ballot_sync(kFull, !s0.busy);
+            i1 = __ballot_sync(kFull, !s1.busy);
         }
-        if (!__any_sync(kFull, busy))
+        if (!__any_sync(kFull, s0.busy || s1.busy))
             break;
 
-        // ---- one unchecked block per busy lane
-        bool park = false;
-        const float sx = x, sy = y;
-        if (busy) {
-            if (fast && a.max_dwell - d >= K) {
+        // ---- one unchecked block on both slots (results of a slot that is
+        //      idle or parks this round are not used)
+        const float sx0 = s0.x, sy0 = s0.y, sx1 = s1.x, sy1 = s1.y;
 #pragma unroll
-                for (int k = 0; k < kUnroll; ++k)
-                    z_update(x, y, cr, ci);
-                if (z_bounded(x, y))
-                    d += K;
-                else
-                    park = true;  // escaped inside this block
-            } else {
-                park = true;      // tail below max_dwell, or |c| near 2
-            }
+        for (int k = 0; k < kUnroll; ++k) {
+            z_update(s0.x, s0.y, s0.cr, s0.ci);
+            z_update(s1.x, s1.y, s1.cr, s1.ci);
+        }
+        bool park0 = false, park1 = false;
+        if (s0.busy) {
+            if (s0.fast && a.max_dwell - s0.d >= K && z_bounded(s0.x, s0.y))
+                s0.d += K;
+            else
+                park0 = true;  // escaped in this block, tail below max_dwell, or |c| near 2
+        }
+        if (s1.busy) {
+            if (s1.fast && a.max_dwell - s1.d >= K && z_bounded(s1.x, s1.y))
+                s1.d += K;
+            else
+                park1 = true;
         }
 
-        // ---- park finished orbits; finish 32 at a time
-        const unsigned pmask = __ballot_sync(kFull, park);
-        if (pmask) {
-            if (park) {
-                const uint32_t slot = parked + (uint32_t)__popc(pmask & lt_mask);
-                qs[slot] = make_float2(sx, sy);
-                qu[slot] = make_uint2(d, pix);
-                busy = false;
+        // ---- park finished orbits (state before this block); finish the
+        //      top 32 parked orbits whenever there are 32
+        const unsigned p0 = __ballot_sync(kFull, park0), p1 = __ballot_sync(kFull, park1);
+        if (p0 | p1) {
+            const uint32_t n0 = (uint32_t)__popc(p0);
+            if (park0) {
+                const uint32_t slot = parked + (uint32_t)__popc(p0 & lt_mask);
+                qs[slot] = make_float2(sx0, sy0);
+                qu[slot] = make_uint2(s0.d, s0.pix);
+                s0.busy = false;
             }
-            parked += (uint32_t)__popc(pmask);
+            if (park1) {
+                const uint32_t slot = parked + n0 + (uint32_t)__popc(p1 & lt_mask);
+                qs[slot] = make_float2(sx1, sy1);
+                qu[slot] = make_uint2(s1.d, s1.pix);
+                s1.busy = false;
+            }
+            parked += n0 + (uint32_t)__popc(p1);
             __syncwarp();
-            if (parked >= 32u) {
-                const float2 s = qs[lane];
-                const uint2 u = qu[lane];
-                const bool mv = lane < parked - 32u;
-                float2 s2 = make_float2(0.f, 0.f);
-                uint2 u2 = make_uint2(0u, 0u);
-                if (mv) {
-                    s2 = qs[32u + lane];
-                    u2 = qu[32u + lane];
-                }
-                __syncwarp();
-                if (mv) {
-                    qs[lane] = s2;
-                    qu[lane] = u2;
-                }
+            while (parked >= 32u) {
                 parked -= 32u;
+                const float2 sv = qs[parked + lane];
+                const uint2 uv = qu[parked + lane];
                 __syncwarp();
-                finish_parked<COUNT>(a, s, u, it);
+                finish_parked<COUNT>(a, sv, uv, it);
                 if (COUNT)
                     ++lpx;
             }
