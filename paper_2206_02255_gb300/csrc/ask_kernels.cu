@@ -595,44 +595,29 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2
         it += d;
 }
 
-// One orbit slot of a lane, walking a run of pixels (a row of a leaf).
+// One orbit slot of a lane.
 struct Slot {
     float x, y, cr, ci;
-    uint32_t d;
-    uint32_t px, py, end;  // current pixel; the run ends before column `end`
+    uint32_t d, pix;
     bool busy, fast;
 };
 
-__device__ __forceinline__ void slot_pixel(Slot &o, const PixelMap &pm)
+__device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t px, uint32_t py)
 {
-    const float2 c = pixel_c(pm, o.px, o.py);
+    const float2 c = pixel_c(pm, px, py);
     o.cr = c.x;
     o.ci = c.y;
     o.x = 0.0f;
     o.y = 0.0f;
     o.d = 0;
+    o.pix = (py << 16) | px;
     o.fast = escape_absorbing(c.x, c.y);
     o.busy = true;
 }
 
-// Park the slot's finished orbit (the state saved before this round's block)
-// and move the slot to the next pixel of its run, if any.
-__device__ __forceinline__ void slot_park(Slot &o, float2 *qs, uint2 *qu, uint32_t slot, float sx,
-                                          float sy, const PixelMap &pm)
-{
-    qs[slot] = make_float2(sx, sy);
-    qu[slot] = make_uint2(o.d, (o.py << 16) | o.px);
-    if (o.px + 1u < o.end) {
-        ++o.px;
-        slot_pixel(o, pm);
-    } else {
-        o.busy = false;
-    }
-}
-
-// Each lane carries two orbit slots, and each slot walks a whole row of a
-// leaf, so taking the next pixel costs a few instructions and no warp-wide
-// coordination; rows are handed out to idle slots once per row.
+// Each lane carries two independent orbits, so one round's bookkeeping
+// (votes, refills, parking) serves two blocks of updates, and the two update
+// chains interleave.
 template <bool COUNT>
 __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs a)
 {
@@ -646,21 +631,21 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
 
     const uint32_t nleaves = min(a.ctr->leaf_count, a.leaf_cap);
     const uint32_t K = (uint32_t)kUnroll;
-    // the warp's current leaf: rows still to hand out
-    uint32_t rows = 0, row_y = 0, xb = 0, xe = 0;
+    // the warp's current leaf: the part still to hand out, as a row-major cursor
+    uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1;
     bool more = true;
     Slot s0, s1;
     s0.busy = s1.busy = false;
     s0.fast = s1.fast = false;
     s0.x = s0.y = s0.cr = s0.ci = s1.x = s1.y = s1.cr = s1.ci = 0.0f;
-    s0.d = s1.d = s0.px = s1.px = s0.py = s1.py = s0.end = s1.end = 0;
+    s0.d = s1.d = s0.pix = s1.pix = 0;
     unsigned long long it = 0, lpx = 0;
 
     for (;;) {
-        // ---- hand rows to idle slots: slot 0 of the idle lanes, then slot 1
+        // ---- refill idle slots: slot 0 of the idle lanes, then slot 1
         unsigned i0 = __ballot_sync(kFull, !s0.busy), i1 = __ballot_sync(kFull, !s1.busy);
         while ((i0 | i1) && more) {
-            if (rows == 0) {
+            if (rem == 0) {
                 uint32_t li = 0;
                 if (lane == 0)
                     li = atomicAdd(&a.ctr->leaf_work, 1u);
@@ -672,36 +657,45 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                 const Region g = unpack_region(a.leaves[li]);
                 if (a.skip_perimeter) {
                     // only the interior; a leaf of side <= 2 is all perimeter
-                    rows = (g.w > 2u && g.h > 2u) ? g.h - 2u : 0u;
-                    row_y = g.y0 + 1u;
-                    xb = g.x0 + 1u;
-                    xe = g.x0 + g.w - 1u;
+                    cw = g.w > 2u ? g.w - 2u : 1u;
+                    rem = (g.w > 2u && g.h > 2u) ? (g.w - 2u) * (g.h - 2u) : 0u;
+                    ox = g.x0 + 1u;
+                    oy = g.y0 + 1u;
                 } else {
-                    rows = g.h;
-                    row_y = g.y0;
-                    xb = g.x0;
-                    xe = g.x0 + g.w;
+                    cw = g.w;
+                    rem = g.w * g.h;
+                    ox = g.x0;
+                    oy = g.y0;
                 }
+                row0 = col0 = 0;
                 continue;
             }
             const uint32_t n0 = (uint32_t)__popc(i0);
-            const uint32_t take = min(n0 + (uint32_t)__popc(i1), rows);
+            const uint32_t take = min(n0 + (uint32_t)__popc(i1), rem);
             const uint32_t r0 = (uint32_t)__popc(i0 & lt_mask);
             const uint32_t r1 = n0 + (uint32_t)__popc(i1 & lt_mask);
             if (!s0.busy && r0 < take) {
-                s0.px = xb;
-                s0.py = row_y + r0;
-                s0.end = xe;
-                slot_pixel(s0, a.pm);
+                uint32_t col = col0 + r0, row = row0;
+                while (col >= cw) {
+                    col -= cw;
+                    ++row;
+                }
+                slot_start(s0, a.pm, ox + col, oy + row);
             }
             if (!s1.busy && r1 < take) {
-                s1.px = xb;
-                s1.py = row_y + r1;
-                s1.end = xe;
-                slot_pixel(s1, a.pm);
+                uint32_t col = col0 + r1, row = row0;
+                while (col >= cw) {
+                    col -= cw;
+                    ++row;
+                }
+                slot_start(s1, a.pm, ox + col, oy + row);
             }
-            row_y += take;
-            rows -= take;
+            col0 += take;
+            while (col0 >= cw) {
+                col0 -= cw;
+                ++row0;
+            }
+            rem -= take;
             i0 = __ballot_sync(kFull, !s0.busy);
             i1 = __ballot_sync(kFull, !s1.busy);
         }
@@ -735,10 +729,18 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
         const unsigned p0 = __ballot_sync(kFull, park0), p1 = __ballot_sync(kFull, park1);
         if (p0 | p1) {
             const uint32_t n0 = (uint32_t)__popc(p0);
-            if (park0)
-                slot_park(s0, qs, qu, parked + (uint32_t)__popc(p0 & lt_mask), sx0, sy0, a.pm);
-            if (park1)
-                slot_park(s1, qs, qu, parked + n0 + (uint32_t)__popc(p1 & lt_mask), sx1, sy1, a.pm);
+            if (park0) {
+                const uint32_t slot = parked + (uint32_t)__popc(p0 & lt_mask);
+                qs[slot] = make_float2(sx0, sy0);
+                qu[slot] = make_uint2(s0.d, s0.pix);
+                s0.busy = false;
+            }
+            if (park1) {
+                const uint32_t slot = parked + n0 + (uint32_t)__popc(p1 & lt_mask);
+                qs[slot] = make_float2(sx1, sy1);
+                qu[slot] = make_uint2(s1.d, s1.pix);
+                s1.busy = false;
+            }
             parked += n0 + (uint32_t)__popc(p1);
             __syncwarp();
             while (parked >= 32u) {
