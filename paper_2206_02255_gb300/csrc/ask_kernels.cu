@@ -309,7 +309,7 @@ __device__ __forceinline__ void chunk_exact(const LevelArgs &a, const Region &g,
 // large region).
 // ---------------------------------------------------------------------------
 template <bool COUNT>
-__global__ void __launch_bounds__(256, 4) level_kernel(LevelArgs a)
+__global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
 {
     extern __shared__ uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
@@ -331,15 +331,13 @@ __global__ void __launch_bounds__(256, 4) level_kernel(LevelArgs a)
     // magnitude: a uniform perimeter inside the set runs to max_dwell); the
     // next index is requested while the current item runs, so the atomic's
     // round trip stays off the critical path
-    uint32_t next = 0;
-    if (lane == 0)
-        next = atomicAdd(&a.ctr->work[a.level], 1u);
     for (;;) {
-        const uint32_t t = __shfl_sync(kFull, next, 0);
+        uint32_t t = 0;
+        if (lane == 0)
+            t = atomicAdd(&a.ctr->work[a.level], 1u);
+        t = __shfl_sync(kFull, t, 0);
         if (t >= items)
             break;
-        if (lane == 0)
-            next = atomicAdd(&a.ctr->work[a.level], 1u);
         const uint32_t region = (chunks == 1u) ? t : t / chunks;
         const uint2 e = a.olt_in[region];
         const Region g = unpack_region(e);
