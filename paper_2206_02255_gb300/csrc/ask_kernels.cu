@@ -552,10 +552,11 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 // ---------------------------------------------------------------------------
 constexpr int kRefillWarps = 8;    // warps per CTA
 constexpr uint32_t kParkCap = 128; // parked orbits per warp (< 32 + 2 * 32)
+constexpr int kLeafUnroll = 32;    // updates per unchecked block (a power of two)
 
 // Exact dwell of a parked orbit: state (x, y) after d updates, that state
 // known to pass the test, and "escaped, or d >= max_dwell" known to hold
-// kUnroll updates later.  Points where escape is not absorbing take the
+// kLeafUnroll updates later.  Points where escape is not absorbing take the
 // tested loop instead.
 template <bool COUNT>
 __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2 u,
@@ -574,7 +575,7 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2
         // invariant: count d passes (d < max_dwell) and the predicate holds
         // at d + 2h; halve h until the first count where it holds is d + 1
 #pragma unroll
-        for (uint32_t h = (uint32_t)kUnroll / 2u; h >= 1u; h >>= 1) {
+        for (uint32_t h = (uint32_t)kLeafUnroll / 2u; h >= 1u; h >>= 1) {
             float tx = x, ty = y;
 #pragma unroll
             for (uint32_t k = 0; k < h; ++k)
@@ -591,6 +592,14 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2
     a.map[(size_t)py * a.n + px] = d;
     if (COUNT)
         it += d;
+}
+
+// floor(q / w) for q < 2^22 given inv_w = 1/w rounded to float: (q + 1/2)/w
+// lies at least 1/(2w) away from an integer, far more than the rounding of
+// the two float operations, so truncation gives the exact quotient.
+__device__ __forceinline__ uint32_t rows_in(uint32_t q, float inv_w)
+{
+    return __float2uint_rz(__fmul_rz(__uint2float_rn(q) + 0.5f, inv_w));
 }
 
 // One orbit slot of a lane.
@@ -628,9 +637,10 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
     uint32_t parked = 0;  // warp-uniform
 
     const uint32_t nleaves = min(a.ctr->leaf_count, a.leaf_cap);
-    const uint32_t K = (uint32_t)kUnroll;
+    const uint32_t K = (uint32_t)kLeafUnroll;
     // the warp's current leaf: the part still to hand out, as a row-major cursor
     uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1;
+    float inv_cw = 1.0f;
     bool more = true;
     Slot s0, s1;
     s0.busy = s1.busy = false;
@@ -666,6 +676,7 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                     oy = g.y0;
                 }
                 row0 = col0 = 0;
+                inv_cw = 1.0f / (float)cw;
                 continue;
             }
             const uint32_t n0 = (uint32_t)__popc(i0);
@@ -673,25 +684,17 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             const uint32_t r0 = (uint32_t)__popc(i0 & lt_mask);
             const uint32_t r1 = n0 + (uint32_t)__popc(i1 & lt_mask);
             if (!s0.busy && r0 < take) {
-                uint32_t col = col0 + r0, row = row0;
-                while (col >= cw) {
-                    col -= cw;
-                    ++row;
-                }
-                slot_start(s0, a.pm, ox + col, oy + row);
+                const uint32_t q = col0 + r0, dr = rows_in(q, inv_cw);
+                slot_start(s0, a.pm, ox + q - dr * cw, oy + row0 + dr);
             }
             if (!s1.busy && r1 < take) {
-                uint32_t col = col0 + r1, row = row0;
-                while (col >= cw) {
-                    col -= cw;
-                    ++row;
-                }
-                slot_start(s1, a.pm, ox + col, oy + row);
+                const uint32_t q = col0 + r1, dr = rows_in(q, inv_cw);
+                slot_start(s1, a.pm, ox + q - dr * cw, oy + row0 + dr);
             }
-            col0 += take;
-            while (col0 >= cw) {
-                col0 -= cw;
-                ++row0;
+            {
+                const uint32_t q = col0 + take, dr = rows_in(q, inv_cw);
+                col0 = q - dr * cw;
+                row0 += dr;
             }
             rem -= take;
             i0 = __ballot_sync(kFull, !s0.busy);
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
         //      idle or parks this round are not used)
         const float sx0 = s0.x, sy0 = s0.y, sx1 = s1.x, sy1 = s1.y;
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) {
+        for (int k = 0; k < kLeafUnroll; ++k) {
             z_update(s0.x, s0.y, s0.cr, s0.ci);
             z_update(s1.x, s1.y, s1.cr, s1.ci);
         }
