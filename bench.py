@@ -31,6 +31,29 @@ if ROOT not in sys.path:
 
 METRIC = "Gpixels/s and dwell-iter/s (ASK vs exhaustive vs CDP2, 1 GB300); p50/p99 latency"
 UNIT = "Gpixels/s"
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic_ask_n16384_d2048.json")
+KERNEL_SOURCES = ["paper_2206_02255_gb300/csrc/ask_kernels.cu",
+                  "paper_2206_02255_gb300/csrc/ask_device.cuh",
+                  "paper_2206_02255_gb300/csrc/ask_internal.h"]
+
+
+def recorded_traffic(kernel_key, workload):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu record,
+    or None if the record is for another workload or the kernels changed
+    since it was taken."""
+    import hashlib
+    try:
+        rec = json.load(open(TRAFFIC_RECORD))
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["kernel_source_sha256"] or not rec["workload"].startswith(workload):
+            return None
+        return rec["per_launch_dram_bytes"].get(kernel_key)
+    except Exception:
+        return None
+
+
 # z <- z^2 + c with the library's rounding: fma(-zi, zi, cr), fma(zr, zr, .),
 # zr + zr, fma(., zi, ci); the |z|^2 test is amortised over a block of updates
 FP32_OPS_PER_ITER = 4
@@ -325,8 +348,10 @@ def run_gpu(args):
         pass
     # one dwell iteration needs at least 3 FFMA + 1 FADD on the FP32 pipe
     peak = sms * 128 * f_mhz * 1e6 / FP32_OPS_PER_ITER / 1e9
+    key = "leaf_refill_kernel" if dom == "leaf" else "level_kernel_" + dom
+    traffic = recorded_traffic(key, C["name"]) if (g, r, B) == (16, 4, 16) else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "Gdwell-iter/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Gdwell-iter/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / %d FP32 ops per iteration"
                               % (sms, f_mhz, FP32_OPS_PER_ITER)}
     if clk and clk.get("sm_mhz"):
