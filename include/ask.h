@@ -171,6 +171,38 @@ ask_status ask_render_host(ask_ctx *ctx, ask_method method, const ask_window *wi
                            uint32_t n, uint32_t max_dwell, const ask_params *params,
                            uint32_t *h_dwell, void *stream, ask_stats *stats);
 
+/* One frame of a batch: its own window, size, dwell cap, subdivision
+ * parameters and caller-owned device output (n*n uint32, 16-byte aligned). */
+typedef struct {
+    ask_window window;
+    uint32_t n, max_dwell;
+    uint32_t g, r, B;
+    uint32_t pad_;
+    uint32_t *d_dwell;
+} ask_frame;
+
+/* Render `nframes` frames of different sizes, windows and dwell caps with
+ * one chain of launches for the whole batch: an init kernel, one persistent
+ * level kernel per subdivision depth whose work queue holds the regions of
+ * every frame at that depth, the deferred-fill kernel and one leaf kernel
+ * over the leaves of every frame (ASK, Sec. 5, with region records that name
+ * their frame).  flags: ASK_FLAG_COUNT, ASK_FLAG_EXACT_BORDERS.  Maps are
+ * identical to rendering each frame alone with ask_render.  Asynchronous on
+ * `stream` unless stats != NULL (then it synchronises and sums counts over
+ * the frames).  The context's batch scratch grows as needed. */
+ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes,
+                            uint32_t flags, void *stream, ask_stats *stats);
+
+/* A batch render captured as a CUDA graph with its own scratch: replaying it
+ * renders the same frames into the same buffers with one graph launch.
+ * flags: ASK_FLAG_EXACT_BORDERS only.  Creation allocates and synchronises
+ * `stream`; launches do neither. */
+typedef struct ask_graph ask_graph;
+ask_status ask_graph_create_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes,
+                                  uint32_t flags, void *stream, ask_graph **out);
+ask_status ask_graph_launch(ask_graph *graph, void *stream);
+void ask_graph_destroy(ask_graph *graph);
+
 /* Synchronise `stream`, then sum the device times recorded by renders made
  * with ASK_FLAG_TIMING since the previous call into *out and forget them.
  * The renders must all have been issued on `stream` (or be complete). */

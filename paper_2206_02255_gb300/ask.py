@@ -84,6 +84,12 @@ class Timing(ctypes.Structure):
                 "ms_fill": self.ms_fill}
 
 
+class Frame(ctypes.Structure):
+    _fields_ = [("window", Window), ("n", ctypes.c_uint32), ("max_dwell", ctypes.c_uint32),
+                ("g", ctypes.c_uint32), ("r", ctypes.c_uint32), ("B", ctypes.c_uint32),
+                ("pad_", ctypes.c_uint32), ("d_dwell", ctypes.c_void_p)]
+
+
 class AskError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(message)
@@ -111,6 +117,13 @@ SIGNATURES = {
                                        ctypes.c_uint32, _P(ctypes.c_uint32)]),
     "ask_render_noalloc": (ctypes.c_int, [_P(Window), ctypes.c_uint32, ctypes.c_uint32,
                                           _P(Params), ctypes.c_void_p, ctypes.c_void_p]),
+    "ask_render_batch": (ctypes.c_int, [ctypes.c_void_p, _P(Frame), ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_void_p, _P(Stats)]),
+    "ask_graph_create_batch": (ctypes.c_int, [ctypes.c_void_p, _P(Frame), ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_void_p,
+                                              _P(ctypes.c_void_p)]),
+    "ask_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ask_graph_destroy": (None, [ctypes.c_void_p]),
     "ask_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "ask_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ask_version": (ctypes.c_char_p, []),
@@ -156,6 +169,32 @@ def plan_levels(n, g, r, B):
         raise AskError(st, "ask_plan_levels(%d, %d, %d, %d): %s" % (n, g, r, B, status_str(st)))
     L = levels.value
     return list(sides[:L]), list(regs[:L])
+
+
+class Graph:
+    """A captured batch render (``ask_graph``); ``launch`` replays it."""
+
+    def __init__(self, handle, device):
+        self._h = handle
+        self.device = device
+
+    def launch(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = lib().ask_graph_launch(self._h, ctypes.c_void_p(s.cuda_stream))
+        if st != OK:
+            raise AskError(st, "ask_graph_launch: %s" % status_str(st))
+
+    def close(self):
+        if self._h:
+            lib().ask_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def render_noalloc(window, n, max_dwell, params, out, stream=None):
@@ -293,6 +332,47 @@ class Context:
         if st != OK:
             self._raise(st, "ask_timing_read")
         return t.as_dict()
+
+    def _frames(self, frames):
+        """frames: sequence of dicts with window, n, max_dwell, g, r, B and
+        `out` (a contiguous CUDA tensor of n*n 4-byte elements)."""
+        arr = (Frame * len(frames))()
+        for k, f in enumerate(frames):
+            out = f["out"]
+            n = int(f["n"])
+            if not out.is_cuda or out.numel() != n * n or out.element_size() != 4 or \
+                    not out.is_contiguous():
+                raise ValueError("frame %d: out must be a contiguous CUDA tensor of n*n "
+                                 "4-byte elements" % k)
+            arr[k] = Frame(_window(f["window"]), n, int(f["max_dwell"]), int(f["g"]),
+                           int(f["r"]), int(f["B"]), 0, out.data_ptr())
+        return arr
+
+    def render_batch(self, frames, flags=0, stream=None, stats=False):
+        """Render a batch of frames (see ``_frames``) with one launch chain.
+        Returns None, or the summed stats dict when ``stats`` (synchronises)."""
+        import torch
+        arr = self._frames(frames)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st_obj = Stats() if stats else None
+        st = lib().ask_render_batch(self._h, arr, len(frames), flags,
+                                    ctypes.c_void_p(s.cuda_stream),
+                                    ctypes.byref(st_obj) if st_obj is not None else None)
+        if st != OK:
+            self._raise(st, "ask_render_batch")
+        return st_obj.as_dict() if stats else None
+
+    def graph_batch(self, frames, flags=0, stream=None):
+        """Capture a batch render as a CUDA graph (see :class:`Graph`)."""
+        import torch
+        arr = self._frames(frames)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = lib().ask_graph_create_batch(self._h, arr, len(frames), flags,
+                                          ctypes.c_void_p(s.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            self._raise(st, "ask_graph_create_batch")
+        return Graph(h, self.device)
 
     def check(self, stream=None):
         sptr = stream.cuda_stream if stream is not None else 0

@@ -12,8 +12,27 @@
 
 #include "ask_internal.h"
 
+// Device scratch of a batch render (owned by a context, or by a graph).
+struct BatchBuffers {
+    uint4 *olt[2] = {nullptr, nullptr};  // region records with frame ids
+    uint64_t olt_cap = 0;
+    uint4 *leaves = nullptr;
+    uint64_t leaf_cap = 0;
+    uint4 *rst[2] = {nullptr, nullptr};
+    uint64_t rst_cap = 0;
+    uint4 *fills = nullptr;
+    uint64_t fill_cap = 0;
+    ask::FrameDesc *frames = nullptr;    // device frame table
+    uint64_t frames_cap = 0;
+    ask::DevCounters *ctr = nullptr;     // not owned when it is the context's
+};
+
 struct ask_ctx {
     ask::DeviceInfo dev;
+    BatchBuffers batch;
+    ask::FrameDesc *h_frames = nullptr;  // pinned staging of the frame table
+    uint64_t h_frames_cap = 0;
+    cudaEvent_t frames_copied = nullptr; // the staging buffer may be rewritten after it
     // region tables (double buffered), leaf list, counters
     uint2 *olt[2] = {nullptr, nullptr};
     uint64_t olt_cap = 0;
@@ -44,6 +63,13 @@ struct ask_ctx {
     uint32_t ring_dropped = 0;
     size_t cdp_pending = 0;
     char err[256];
+};
+
+struct ask_graph {
+    int device = 0;
+    BatchBuffers buf;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace ask {
@@ -511,7 +537,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.fill_cap = (uint32_t)ctx->fill_cap;
         a.exact_last = exact ? 1u : 0u;
         a.ctr = ctx->ctr;
-        if ((e = launch_level(a, count, sms, s)) != cudaSuccess)
+        if ((e = launch_level(a, count, false, sms, s)) != cudaSuccess)
             return cuda_err(ctx, e, "level kernel");
         ++launches;
         mk.at(2 + (int)i, s);
@@ -524,7 +550,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         f.fill_cap = (uint32_t)ctx->fill_cap;
         f.max_rows = plan.side[0];
         f.ctr = ctx->ctr;
-        if ((e = launch_fill(f, sms, s)) != cudaSuccess)
+        if ((e = launch_fill(f, false, sms, s)) != cudaSuccess)
             return cuda_err(ctx, e, "fill kernel");
         ++launches;
     }
@@ -539,8 +565,8 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     la.leaf_cap = (uint32_t)ctx->leaf_cap;
     la.skip_perimeter = exact ? 1u : 0u;
     la.ctr = ctx->ctr;
-    if ((e = launch_leaf(la, p.block_x, p.block_y, count, (p.flags & ASK_FLAG_LEAF_TILED) != 0, sms,
-                         s)) != cudaSuccess)
+    if ((e = launch_leaf(la, p.block_x, p.block_y, count, (p.flags & ASK_FLAG_LEAF_TILED) != 0, false,
+                         sms, s)) != cudaSuccess)
         return cuda_err(ctx, e, "leaf kernel");
     ++launches;
     mk.at(3 + (int)L, s);
@@ -572,6 +598,234 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         stats->leaf_iterations = c.leaf_iters;
         stats->kernel_launches = launches;
     }
+    return ASK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+    std::vector<FrameDesc> desc;
+    uint32_t L = 0;                       // deepest level over the frames
+    uint32_t chunks[ASK_MAX_LEVELS] = {};  // chunks per region at each level (max over frames)
+    uint64_t olt_need = 0, leaf_need = 0, rst_need = 0, fill_need = 0;
+    uint32_t total0 = 0, max_rows = 0;
+};
+
+ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, uint32_t flags,
+                      uint32_t allowed_flags, BatchPlan &bp)
+{
+    if (!frames || nframes == 0 || nframes > (1u << 20))
+        return set_err(ctx, ASK_EINVAL, "a batch needs 1 to 2^20 frames");
+    if (flags & ~allowed_flags)
+        return set_err(ctx, ASK_EINVAL, "unsupported flags 0x%x for a batch", flags);
+    bp.desc.resize(nframes);
+    uint64_t level_regions[ASK_MAX_LEVELS] = {};
+    uint64_t total0 = 0;
+    for (uint32_t f = 0; f < nframes; ++f) {
+        const ask_frame &fr = frames[f];
+        ask_params p{};
+        p.g = fr.g;
+        p.r = fr.r;
+        p.B = fr.B;
+        p.block_x = 16;
+        p.block_y = 16;
+        ask_params eff;
+        ask_status st = check_args(ctx, ASK_METHOD_ASK, &fr.window, fr.n, fr.max_dwell, &p, &eff);
+        if (st != ASK_OK) {
+            char why[sizeof(ctx->err)];
+            std::memcpy(why, ctx->err, sizeof(why));
+            return set_err(ctx, st, "frame %u: %s", f, why);
+        }
+        if (!fr.d_dwell || ((uintptr_t)fr.d_dwell & 15u))
+            return set_err(ctx, ASK_EINVAL, "frame %u: d_dwell must be 16-byte aligned", f);
+        LevelPlan plan;
+        if (!make_plan(fr.n, fr.g, fr.r, fr.B, &plan))
+            return set_err(ctx, ASK_EINVAL, "frame %u: no valid subdivision plan", f);
+        FrameDesc &d = bp.desc[f];
+        std::memset(&d, 0, sizeof(d));
+        d.map = fr.d_dwell;
+        d.pm = pixel_map(&fr.window, fr.n);
+        d.n = fr.n;
+        d.max_dwell = fr.max_dwell;
+        d.r = fr.r;
+        d.levels = plan.levels;
+        d.s0 = plan.side[0];
+        d.axis0 = plan.axis0;
+        d.olt0_offset = (uint32_t)total0;
+        for (uint32_t i = 0; i < plan.levels; ++i) {
+            d.side[i] = plan.side[i];
+            level_regions[i] += plan.max_regions[i];
+            if (plan.chunks[i] > bp.chunks[i])
+                bp.chunks[i] = plan.chunks[i];
+            if ((uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
+                bp.fill_need += plan.max_regions[i];
+        }
+        bp.leaf_need += plan.max_regions[plan.levels - 1];
+        total0 += (uint64_t)plan.axis0 * plan.axis0;
+        if (plan.levels > bp.L)
+            bp.L = plan.levels;
+        if (plan.side[0] > bp.max_rows)
+            bp.max_rows = plan.side[0];
+    }
+    for (uint32_t i = 0; i < bp.L; ++i) {
+        if (level_regions[i] * bp.chunks[i] >= 0xffffffffull)
+            return set_err(ctx, ASK_EINVAL, "batch too large: level %u holds too many work items", i);
+        if (level_regions[i] > bp.olt_need)
+            bp.olt_need = level_regions[i];
+        if (bp.chunks[i] > 1u && level_regions[i] > bp.rst_need)
+            bp.rst_need = level_regions[i];
+    }
+    if (bp.leaf_need >= 0xffffffffull || bp.fill_need >= 0xffffffffull)
+        return set_err(ctx, ASK_EINVAL, "batch too large");
+    bp.total0 = (uint32_t)total0;
+    return ASK_OK;
+}
+
+ask_status reserve_batch(ask_ctx *ctx, BatchBuffers &b, const BatchPlan &bp, bool own_counters)
+{
+    ask_status st;
+    if (bp.olt_need > b.olt_cap) {
+        uint64_t c0 = b.olt_cap, c1 = b.olt_cap;
+        if ((st = grow(ctx, &b.olt[0], &c0, bp.olt_need, "cudaMalloc(batch regions)")) != ASK_OK ||
+            (st = grow(ctx, &b.olt[1], &c1, bp.olt_need, "cudaMalloc(batch regions)")) != ASK_OK) {
+            b.olt_cap = 0;
+            return st;
+        }
+        b.olt_cap = bp.olt_need;
+    }
+    if (bp.rst_need > b.rst_cap) {
+        uint64_t c0 = b.rst_cap, c1 = b.rst_cap;
+        if ((st = grow(ctx, &b.rst[0], &c0, bp.rst_need, "cudaMalloc(batch query state)")) != ASK_OK ||
+            (st = grow(ctx, &b.rst[1], &c1, bp.rst_need, "cudaMalloc(batch query state)")) != ASK_OK) {
+            b.rst_cap = 0;
+            return st;
+        }
+        b.rst_cap = bp.rst_need;
+    }
+    if ((st = grow(ctx, &b.leaves, &b.leaf_cap, bp.leaf_need, "cudaMalloc(batch leaves)")) != ASK_OK)
+        return st;
+    if ((st = grow(ctx, &b.fills, &b.fill_cap, bp.fill_need, "cudaMalloc(batch fills)")) != ASK_OK)
+        return st;
+    if ((st = grow(ctx, &b.frames, &b.frames_cap, (uint64_t)bp.desc.size(), "cudaMalloc(frame table)")) !=
+        ASK_OK)
+        return st;
+    if (own_counters && !b.ctr) {
+        cudaError_t e = cudaMalloc(&b.ctr, sizeof(DevCounters));
+        if (e == cudaSuccess)
+            e = cudaMemset(b.ctr, 0, sizeof(DevCounters));
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaMalloc(batch counters)");
+    }
+    return ASK_OK;
+}
+
+void free_batch(BatchBuffers &b, bool own_counters)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (b.olt[k])
+            cudaFree(b.olt[k]);
+        if (b.rst[k])
+            cudaFree(b.rst[k]);
+    }
+    if (b.leaves)
+        cudaFree(b.leaves);
+    if (b.fills)
+        cudaFree(b.fills);
+    if (b.frames)
+        cudaFree(b.frames);
+    if (own_counters && b.ctr)
+        cudaFree(b.ctr);
+    b = BatchBuffers();
+}
+
+// The launch chain of a batch; the frame table must already be on the device.
+ask_status enqueue_batch(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &bp, uint32_t flags,
+                         cudaStream_t s, uint32_t *launches)
+{
+    const int sms = ctx->dev.sms;
+    const bool count = (flags & ASK_FLAG_COUNT) != 0;
+    const bool exact = (flags & ASK_FLAG_EXACT_BORDERS) != 0;
+    const uint32_t nframes = (uint32_t)bp.desc.size();
+    cudaError_t e;
+    if ((e = launch_init_batch(b.olt[0], bp.chunks[0] > 1u ? b.rst[0] : nullptr, b.ctr, b.frames, nframes,
+                               bp.total0, s)) != cudaSuccess)
+        return cuda_err(ctx, e, "batch init kernel");
+    uint32_t n_launch = 1;
+    for (uint32_t i = 0; i < bp.L; ++i) {
+        LevelArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.level = i;
+        a.olt_in = b.olt[i & 1];
+        a.olt_out = b.olt[(i + 1) & 1];
+        a.olt_cap = (uint32_t)b.olt_cap;
+        a.chunks = bp.chunks[i];
+        a.next_chunks = (i + 1 < bp.L) ? bp.chunks[i + 1] : 1u;
+        a.rst_in = b.rst[i & 1];
+        a.rst_out = b.rst[(i + 1) & 1];
+        a.leaves = b.leaves;
+        a.leaf_cap = (uint32_t)b.leaf_cap;
+        a.fills = bp.fill_need ? b.fills : nullptr;
+        a.fill_cap = (uint32_t)b.fill_cap;
+        a.exact_last = exact ? 1u : 0u;
+        a.frames = b.frames;
+        a.ctr = b.ctr;
+        if ((e = launch_level(a, count, true, sms, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "batch level kernel");
+        ++n_launch;
+    }
+    if (bp.fill_need) {
+        FillArgs f;
+        std::memset(&f, 0, sizeof(f));
+        f.fills = b.fills;
+        f.fill_cap = (uint32_t)b.fill_cap;
+        f.max_rows = bp.max_rows;
+        f.frames = b.frames;
+        f.ctr = b.ctr;
+        if ((e = launch_fill(f, true, sms, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "batch fill kernel");
+        ++n_launch;
+    }
+    LeafArgs la;
+    std::memset(&la, 0, sizeof(la));
+    la.leaves = b.leaves;
+    la.leaf_cap = (uint32_t)b.leaf_cap;
+    la.skip_perimeter = exact ? 1u : 0u;
+    la.frames = b.frames;
+    la.ctr = b.ctr;
+    if ((e = launch_leaf(la, 16, 16, count, false, true, sms, s)) != cudaSuccess)
+        return cuda_err(ctx, e, "batch leaf kernel");
+    ++n_launch;
+    if (launches)
+        *launches = n_launch;
+    return ASK_OK;
+}
+
+// Copy the frame table through the context's pinned staging buffer.
+ask_status upload_frames(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &bp, cudaStream_t s)
+{
+    const uint64_t nf = bp.desc.size();
+    cudaError_t e;
+    if (ctx->frames_copied && (e = cudaEventSynchronize(ctx->frames_copied)) != cudaSuccess)
+        return cuda_err(ctx, e, "waiting for the previous frame-table copy");
+    if (nf > ctx->h_frames_cap) {
+        if (ctx->h_frames)
+            cudaFreeHost(ctx->h_frames);
+        ctx->h_frames = nullptr;
+        ctx->h_frames_cap = 0;
+        if ((e = cudaMallocHost(&ctx->h_frames, nf * sizeof(FrameDesc))) != cudaSuccess)
+            return cuda_err(ctx, e, "cudaMallocHost(frame table)");
+        ctx->h_frames_cap = nf;
+    }
+    if (!ctx->frames_copied && (e = cudaEventCreateWithFlags(&ctx->frames_copied, cudaEventDisableTiming)) !=
+                                   cudaSuccess)
+        return cuda_err(ctx, e, "cudaEventCreate");
+    std::memcpy(ctx->h_frames, bp.desc.data(), nf * sizeof(FrameDesc));
+    if ((e = cudaMemcpyAsync(b.frames, ctx->h_frames, nf * sizeof(FrameDesc), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_err(ctx, e, "copying the frame table");
+    if ((e = cudaEventRecord(ctx->frames_copied, s)) != cudaSuccess)
+        return cuda_err(ctx, e, "cudaEventRecord");
     return ASK_OK;
 }
 
@@ -640,6 +894,11 @@ void ask_ctx_destroy(ask_ctx *ctx)
             cudaFree(ctx->rst[b]);
     if (ctx->fills)
         cudaFree(ctx->fills);
+    free_batch(ctx->batch, false);
+    if (ctx->h_frames)
+        cudaFreeHost(ctx->h_frames);
+    if (ctx->frames_copied)
+        cudaEventDestroy(ctx->frames_copied);
     if (ctx->ctr)
         cudaFree(ctx->ctr);
     if (ctx->h_ctr)
@@ -787,6 +1046,144 @@ ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
     ctx->ring_tail = ctx->ring_head;
     ctx->ring_dropped = 0;
     return ASK_OK;
+}
+
+ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, uint32_t flags,
+                            void *stream, ask_stats *stats)
+{
+    if (!ctx)
+        return ASK_EINVAL;
+    BatchPlan bp;
+    ask_status st = plan_batch(ctx, frames, nframes, flags, ASK_FLAG_COUNT | ASK_FLAG_EXACT_BORDERS, bp);
+    if (st != ASK_OK)
+        return st;
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    if ((st = ensure_counters(ctx)) != ASK_OK)
+        return st;
+    ctx->batch.ctr = ctx->ctr;
+    if ((st = reserve_batch(ctx, ctx->batch, bp, false)) != ASK_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        if ((st = ensure_events(ctx)) != ASK_OK)
+            return st;
+    }
+    if ((st = upload_frames(ctx, ctx->batch, bp, s)) != ASK_OK)
+        return st;
+    if (stats)
+        cudaEventRecord(ctx->ev[0], s);
+    uint32_t launches = 0;
+    if ((st = enqueue_batch(ctx, ctx->batch, bp, flags, s, &launches)) != ASK_OK)
+        return st;
+    if (stats) {
+        cudaEventRecord(ctx->ev[1], s);
+        if ((st = read_counters(ctx, s)) != ASK_OK)
+            return st;
+        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[1]);
+        const DevCounters &c = *ctx->h_ctr;
+        stats->levels = bp.L;
+        for (uint32_t i = 0; i < bp.L; ++i) {
+            stats->regions_per_level[i] = c.count[i];
+            stats->fills_per_level[i] = c.fills[i];
+            stats->subdivisions_per_level[i] = c.subdivs[i];
+            stats->iterations_per_level[i] = c.level_iters[i];
+        }
+        stats->leaves = c.leaf_count;
+        stats->fill_pixels = c.fill_pixels;
+        stats->leaf_pixels = c.leaf_pixels;
+        stats->border_pixels = c.border_pixels;
+        stats->iterations = c.iterations;
+        stats->leaf_iterations = c.leaf_iters;
+        stats->kernel_launches = launches;
+    }
+    return ASK_OK;
+}
+
+ask_status ask_graph_create_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes,
+                                  uint32_t flags, void *stream, ask_graph **out)
+{
+    if (!ctx || !out)
+        return ASK_EINVAL;
+    *out = nullptr;
+    BatchPlan bp;
+    ask_status st = plan_batch(ctx, frames, nframes, flags, ASK_FLAG_EXACT_BORDERS, bp);
+    if (st != ASK_OK)
+        return st;
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    ask_graph *g = new (std::nothrow) ask_graph();
+    if (!g)
+        return ASK_ENOMEM;
+    g->device = ctx->dev.device;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((st = reserve_batch(ctx, g->buf, bp, true)) != ASK_OK ||
+        (st = upload_frames(ctx, g->buf, bp, s)) != ASK_OK) {
+        free_batch(g->buf, true);
+        delete g;
+        return st;
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        free_batch(g->buf, true);
+        delete g;
+        return cuda_err(ctx, e, "cudaStreamSynchronize");
+    }
+    // capture on a private stream so the caller's stream is never in capture mode
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+        free_batch(g->buf, true);
+        delete g;
+        return cuda_err(ctx, e, "cudaStreamCreate");
+    }
+    st = ASK_OK;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        st = cuda_err(ctx, e, "cudaStreamBeginCapture");
+    } else {
+        const ask_status est = enqueue_batch(ctx, g->buf, bp, flags, cs, nullptr);
+        e = cudaStreamEndCapture(cs, &g->graph);
+        if (est != ASK_OK)
+            st = est;
+        else if (e != cudaSuccess)
+            st = cuda_err(ctx, e, "cudaStreamEndCapture");
+        else if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+            st = cuda_err(ctx, e, "cudaGraphInstantiate");
+    }
+    cudaStreamDestroy(cs);
+    if (st != ASK_OK) {
+        if (g->exec)
+            cudaGraphExecDestroy(g->exec);
+        if (g->graph)
+            cudaGraphDestroy(g->graph);
+        free_batch(g->buf, true);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return ASK_OK;
+}
+
+ask_status ask_graph_launch(ask_graph *g, void *stream)
+{
+    if (!g || !g->exec)
+        return ASK_EINVAL;
+    if (cudaSetDevice(g->device) != cudaSuccess)
+        return ASK_ECUDA;
+    return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? ASK_OK : ASK_ECUDA;
+}
+
+void ask_graph_destroy(ask_graph *g)
+{
+    if (!g)
+        return;
+    cudaSetDevice(g->device);
+    if (g->exec)
+        cudaGraphExecDestroy(g->exec);
+    if (g->graph)
+        cudaGraphDestroy(g->graph);
+    free_batch(g->buf, true);
+    delete g;
 }
 
 ask_status ask_check(ask_ctx *ctx, void *stream)

@@ -70,61 +70,82 @@ cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t m
 cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
                         uint32_t axis0, cudaStream_t s);
 
+// One frame of a batch, resident on the device.  Region records of a batch
+// are uint4 {x0 | y0 << 16, (w-1) | (h-1) << 16, frame, 0}.
+struct FrameDesc {
+    uint32_t *map;        // the frame's output map
+    PixelMap pm;
+    uint32_t n, max_dwell, r, levels;
+    uint32_t s0, axis0;   // level-0 side and non-empty regions per axis
+    uint32_t olt0_offset; // first level-0 record of this frame
+    uint32_t pad_;
+    uint32_t side[ASK_MAX_LEVELS];  // region side at each level
+};
+
 struct LevelArgs {
+    // single frame (ignored by batch launches, which read the frame table)
     uint32_t *map;
     uint32_t n;
     PixelMap pm;
     uint32_t max_dwell;
-    uint32_t level;
     uint32_t side;        // nominal side of this level's regions
     uint32_t split;       // non-uniform regions split (else become leaves)
     uint32_t child_side;  // ceil(side / r)
     uint32_t r;
-    const uint2 *olt_in;
-    uint2 *olt_out;
+    // both
+    uint32_t level;
+    const void *olt_in;   // uint2 records (single frame) or uint4 records (batch)
+    void *olt_out;
     uint32_t olt_cap;     // capacity of both region tables
     uint32_t chunks;      // perimeter chunks per region at this level (1 = one warp per region)
     uint32_t next_chunks; // chunks per region at the next level
     uint4 *rst_in;        // per-region query state of this level (chunks > 1)
     uint4 *rst_out;       // state of the next level's regions, set when they are appended
-    uint2 *leaves;
+    void *leaves;         // leaf records, same type as the region records
     uint32_t leaf_cap;
-    uint4 *fills;         // deferred fills (region record, dwell); NULL = fill in place
+    uint4 *fills;         // deferred fills (region, dwell, frame); NULL = fill in place
     uint32_t fill_cap;
     uint32_t exact_last;  // last level: evaluate whole perimeters and write them
+    const FrameDesc *frames;  // batch: the frame table
     DevCounters *ctr;
 };
 // Perimeter pixels per work item of a level kernel.
 constexpr uint32_t kChunkPx = 128;
 // Uniform regions larger than this are filled by the fill kernel.
 constexpr uint32_t kInPlaceFillArea = 16384;
-cudaError_t launch_level(const LevelArgs &a, bool count, int sms, cudaStream_t s);
+cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cudaStream_t s);
 
 struct FillArgs {
-    uint32_t *map;
+    uint32_t *map;        // single frame (batch entries name their frame)
     uint32_t n;
     const uint4 *fills;
     uint32_t fill_cap;
     uint32_t max_rows;    // largest height of a deferred region
+    const FrameDesc *frames;
     DevCounters *ctr;
 };
-cudaError_t launch_fill(const FillArgs &f, int sms, cudaStream_t s);
+cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, cudaStream_t s);
+cudaError_t launch_init_batch(uint4 *olt0, uint4 *rst0, DevCounters *ctr, const FrameDesc *frames,
+                              uint32_t nframes, uint32_t total0, cudaStream_t s);
 
 struct LeafArgs {
+    // single frame (ignored by batch launches)
     uint32_t *map;
     uint32_t n;
     PixelMap pm;
     uint32_t max_dwell;
     uint32_t side;        // nominal side of the leaf regions
-    const uint2 *leaves;
+    // both
+    const void *leaves;   // uint2 (single frame) or uint4 (batch) records
     uint32_t leaf_cap;    // capacity of the leaf list
     uint32_t skip_perimeter;  // leaf perimeters are already in the map
+    const FrameDesc *frames;
     DevCounters *ctr;
 };
 // tiled = false: lane-refill kernel (default); true: one thread per pixel in
-// block_x x block_y tiles
+// block_x x block_y tiles (single frame only)
 cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, bool tiled,
-                        int sms, cudaStream_t s);
+                        bool batch, int sms, cudaStream_t s);
 
 // ---- kernels of ask_cdp2.cu ----------------------------------------------
 struct CdpArgs {

@@ -109,17 +109,81 @@ __global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, 
 }
 
 // ---------------------------------------------------------------------------
+// Region records: uint2 for one frame, uint4 (with the frame id) for a batch.
+// ---------------------------------------------------------------------------
+template <bool BATCH>
+struct Rec;
+template <>
+struct Rec<false> {
+    using T = uint2;
+    static __device__ __forceinline__ Region region(T e) { return unpack_region(e); }
+    static __device__ __forceinline__ uint32_t frame(T) { return 0u; }
+    static __device__ __forceinline__ T child(T, uint2 c) { return c; }
+};
+template <>
+struct Rec<true> {
+    using T = uint4;
+    static __device__ __forceinline__ Region region(T e) { return unpack_region(make_uint2(e.x, e.y)); }
+    static __device__ __forceinline__ uint32_t frame(T e) { return e.z; }
+    static __device__ __forceinline__ T child(T p, uint2 c) { return make_uint4(c.x, c.y, p.z, 0u); }
+};
+
+// The parameters of the frame a region belongs to, at one level.
+struct FView {
+    uint32_t *map;
+    PixelMap pm;
+    uint32_t n, max_dwell, side, child_side, r;
+    bool split;
+};
+
+__device__ __forceinline__ FView view_single(const LevelArgs &a)
+{
+    FView v;
+    v.map = a.map;
+    v.pm = a.pm;
+    v.n = a.n;
+    v.max_dwell = a.max_dwell;
+    v.side = a.side;
+    v.child_side = a.child_side;
+    v.r = a.r;
+    v.split = a.split != 0u;
+    return v;
+}
+
+__device__ __forceinline__ FView view_frame(const FrameDesc *frames, uint32_t f, uint32_t level)
+{
+    const FrameDesc &d = frames[f];
+    FView v;
+    v.map = d.map;
+    v.pm = d.pm;
+    v.n = d.n;
+    v.max_dwell = d.max_dwell;
+    v.r = d.r;
+    v.side = d.side[level];
+    v.child_side = ceil_div_u32(v.side, v.r);
+    v.split = level + 1u < d.levels;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
 // Per-warp record of decided regions, flushed with one atomic per list.
 // ---------------------------------------------------------------------------
+template <bool BATCH>
 struct WarpBatch {
-    uint2 rec;       // lane j: OLT record of the j-th region decided
+    typename Rec<BATCH>::T rec;  // lane j: record of the j-th region decided
     uint32_t kind;   // KIND_*
     uint32_t nchild; // children of a splitting region
     uint32_t dwell;  // dwell of a uniform region filled later
+    uint32_t sc, r;  // child side and split factor of its frame
 };
 
-__device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, uint32_t lane)
+template <bool BATCH>
+__device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH> &b, uint32_t lane)
 {
+    using R = Rec<BATCH>;
+    using T = typename R::T;
+    T *leaves = static_cast<T *>(a.leaves);
+    T *olt_out = static_cast<T *>(a.olt_out);
     DevCounters *ctr = a.ctr;
     const unsigned lt = (1u << lane) - 1u;
     // leaves: ballot + popc gives each leaf its slot
@@ -132,7 +196,7 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, ui
         if (b.kind == KIND_LEAF) {
             const uint32_t slot = base + (uint32_t)__popc(leaf_mask & lt);
             if (slot < a.leaf_cap)
-                a.leaves[slot] = b.rec;
+                leaves[slot] = b.rec;
             else
                 atomicOr(&ctr->error, ERR_LEAF_OVERFLOW);
         }
@@ -147,7 +211,7 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, ui
         if (b.kind == KIND_FILL_LATER) {
             const uint32_t slot = base + (uint32_t)__popc(later_mask & lt);
             if (slot < a.fill_cap)
-                a.fills[slot] = make_uint4(b.rec.x, b.rec.y, b.dwell, 0u);
+                a.fills[slot] = make_uint4(b.rec.x, b.rec.y, b.dwell, R::frame(b.rec));
             else
                 atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
         }
@@ -167,12 +231,12 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch &b, ui
             base = atomicAdd(&ctr->count[a.level + 1], total);
         base = __shfl_sync(kFull, base, 0);
         if (b.nchild) {
-            const Region g = unpack_region(b.rec);
+            const Region g = R::region(b.rec);
             const uint32_t first = base + incl - b.nchild;
             for (uint32_t j = 0; j < b.nchild; ++j) {
                 const uint32_t slot = first + j;
                 if (slot < a.olt_cap) {
-                    a.olt_out[slot] = child_region(g, a.child_side, a.r, j);
+                    olt_out[slot] = R::child(b.rec, child_region(g, b.sc, b.r, j));
                     if (a.next_chunks > 1u)
                         a.rst_out[slot] = make_uint4(kNone, 0u, 0u, 0u);
                 } else {
@@ -212,7 +276,7 @@ __device__ __forceinline__ uint2 read_state(const uint4 *st, uint32_t lane)
 // y = 1 once two dwells are known to differ, z = chunks finished.  Chunks of
 // the same region run on other warps at the same time and stop as soon as
 // one of them has set y.
-__device__ __forceinline__ void chunk_query(const LevelArgs &a, const Region &g, uint32_t k0,
+__device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uint32_t k0,
                                             uint32_t k1, uint4 *st, uint32_t lane,
                                             unsigned long long &it)
 {
@@ -281,7 +345,7 @@ __device__ __forceinline__ void chunk_query(const LevelArgs &a, const Region &g,
 
 // One chunk [k0, k1) of a large last-level region with exact perimeters:
 // every dwell is computed and written; st.x / st.y collect min / max.
-__device__ __forceinline__ void chunk_exact(const LevelArgs &a, const Region &g, uint32_t k0,
+__device__ __forceinline__ void chunk_exact(const FView &a, const Region &g, uint32_t k0,
                                             uint32_t k1, uint4 *st, uint32_t lane,
                                             unsigned long long &it)
 {
@@ -308,30 +372,31 @@ __device__ __forceinline__ void chunk_exact(const LevelArgs &a, const Region &g,
 // Level kernel: one warp per work item (a region, or a perimeter chunk of a
 // large region).
 // ---------------------------------------------------------------------------
-template <bool COUNT>
+template <bool COUNT, bool BATCH>
 __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
 {
+    using R = Rec<BATCH>;
+    using T = typename R::T;
     extern __shared__ uint32_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *stage = smem + (threadIdx.x >> 5) * kWarpStage;
+    const T *olt_in = static_cast<const T *>(a.olt_in);
     const uint32_t count = min(a.ctr->count[a.level], a.olt_cap);
     const uint32_t chunks = a.chunks;
     const uint32_t items = count * chunks;  // the host keeps this below 2^32
-    const bool query = a.split || !a.exact_last;
 
-    WarpBatch b;
-    b.rec = make_uint2(0, 0);
+    WarpBatch<BATCH> b;
+    b.rec = T();
     b.kind = KIND_NONE;
     b.nchild = 0;
     b.dwell = 0;
+    b.sc = b.r = 1u;
     uint32_t j = 0;
     unsigned long long it = 0, bpx = 0, fpx = 0;
 
-    // items are handed out one at a time (their costs differ by orders of
-    // magnitude: a uniform perimeter inside the set runs to max_dwell); the
-    // next index is requested while the current item runs, so the atomic's
-    // round trip stays off the critical path
     for (;;) {
+        // items are handed out one at a time: their costs differ by orders
+        // of magnitude (a uniform perimeter inside the set runs to max_dwell)
         uint32_t t = 0;
         if (lane == 0)
             t = atomicAdd(&a.ctr->work[a.level], 1u);
@@ -339,8 +404,10 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
         if (t >= items)
             break;
         const uint32_t region = (chunks == 1u) ? t : t / chunks;
-        const uint2 e = a.olt_in[region];
-        const Region g = unpack_region(e);
+        const T e = olt_in[region];
+        const Region g = R::region(e);
+        const FView f = BATCH ? view_frame(a.frames, R::frame(e), a.level) : view_single(a);
+        const bool query = f.split || !a.exact_last;
         const uint32_t P = perimeter_size(g.w, g.h);
         bool decided = false, uniform = false;
         uint32_t wv = 0;
@@ -350,7 +417,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
             if (COUNT && lane == 0)
                 bpx += P;
             if (query) {
-                uniform = warp_perimeter_uniform(a.pm, a.max_dwell, g, lane, &wv, it);
+                uniform = warp_perimeter_uniform(f.pm, f.max_dwell, g, lane, &wv, it);
             } else {
                 // last level, exact perimeters staged in shared memory: a leaf
                 // keeps them and the leaf kernel skips them
@@ -358,14 +425,14 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                 for (uint32_t k = lane; k < P; k += 32u) {
                     uint32_t px, py;
                     perimeter_pixel(g, k, px, py);
-                    const float2 c = pixel_c(a.pm, px, py);
-                    const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+                    const float2 c = pixel_c(f.pm, px, py);
+                    const uint32_t d = dwell(c.x, c.y, f.max_dwell);
                     dmin = min(dmin, d);
                     dmax = max(dmax, d);
                     if (k < kWarpStage)
                         stage[k] = d;
                     else
-                        a.map[(size_t)py * a.n + px] = d;  // beyond the stage: write through
+                        f.map[(size_t)py * f.n + px] = d;  // beyond the stage: write through
                     if (COUNT)
                         it += d;
                 }
@@ -378,7 +445,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                     for (uint32_t k = lane; k < staged; k += 32u) {
                         uint32_t px, py;
                         perimeter_pixel(g, k, px, py);
-                        a.map[(size_t)py * a.n + px] = stage[k];
+                        f.map[(size_t)py * f.n + px] = stage[k];
                     }
                 }
             }
@@ -390,9 +457,9 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                 bpx += k1 - k0;
             if (k0 < k1) {
                 if (query)
-                    chunk_query(a, g, k0, k1, st, lane, it);
+                    chunk_query(f, g, k0, k1, st, lane, it);
                 else
-                    chunk_exact(a, g, k0, k1, st, lane, it);
+                    chunk_exact(f, g, k0, k1, st, lane, it);
             }
             // the warp that finishes the region's last chunk decides
             uint32_t last = 0;
@@ -424,29 +491,31 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                 if (a.fills != nullptr && area > kInPlaceFillArea) {
                     kind = KIND_FILL_LATER;
                 } else {
-                    fill_rect(a.map, a.n, g, wv, lane, 32u);
+                    fill_rect(f.map, f.n, g, wv, lane, 32u);
                     kind = KIND_FILL;
                 }
                 if (COUNT && lane == 0)
                     fpx += area;
             } else {
-                kind = a.split ? KIND_SPLIT : KIND_LEAF;
+                kind = f.split ? KIND_SPLIT : KIND_LEAF;
             }
             if (lane == j) {
                 b.rec = e;
                 b.kind = kind;
                 b.dwell = wv;
-                b.nchild = (kind == KIND_SPLIT) ? child_count(g, a.child_side, a.r) : 0u;
+                b.sc = f.child_side;
+                b.r = f.r;
+                b.nchild = (kind == KIND_SPLIT) ? child_count(g, f.child_side, f.r) : 0u;
             }
             __syncwarp();
             if (++j == 32u) {
-                flush_batch(a, b, lane);
+                flush_batch<BATCH>(a, b, lane);
                 j = 0;
             }
         }
     }
     if (j)
-        flush_batch(a, b, lane);
+        flush_batch<BATCH>(a, b, lane);
     if (COUNT) {
         it = warp_sum_u64(it);
         bpx = warp_sum_u64(bpx);
@@ -468,6 +537,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
 // Fill kernel: the large uniform regions, one row per warp item, 128-bit
 // stores; pure HBM writes spread over every SM.
 // ---------------------------------------------------------------------------
+template <bool BATCH>
 __global__ void __launch_bounds__(256) fill_kernel(FillArgs f)
 {
     constexpr uint32_t kBand = 8;  // rows per work item
@@ -488,7 +558,12 @@ __global__ void __launch_bounds__(256) fill_kernel(FillArgs f)
         Region rb = g;
         rb.y0 = g.y0 + row;
         rb.h = min(kBand, g.h - row);
-        fill_rect(f.map, f.n, rb, e.z, lane, 32u);
+        if (BATCH) {
+            const FrameDesc &d = f.frames[e.w];
+            fill_rect(d.map, d.n, rb, e.z, lane, 32u);
+        } else {
+            fill_rect(f.map, f.n, rb, e.z, lane, 32u);
+        }
     }
 }
 
@@ -507,7 +582,7 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
     for (unsigned long long item = blockIdx.x; item < total; item += gridDim.x) {
         const uint32_t leaf = (uint32_t)(item / tiles_per_leaf);
         const uint32_t t = (uint32_t)(item - (unsigned long long)leaf * tiles_per_leaf);
-        const Region g = unpack_region(a.leaves[leaf]);
+        const Region g = unpack_region(static_cast<const uint2 *>(a.leaves)[leaf]);
         const uint32_t ty = t / tiles_x, tx = t - ty * tiles_x;
         const uint32_t px = g.x0 + tx * blockDim.x + threadIdx.x;
         const uint32_t py = g.y0 + ty * blockDim.y + threadIdx.y;
@@ -554,24 +629,51 @@ constexpr int kRefillWarps = 8;    // warps per CTA
 constexpr uint32_t kParkCap = 128; // parked orbits per warp (< 32 + 2 * 32)
 constexpr int kLeafUnroll = 32;    // updates per unchecked block (a power of two)
 
+// The output and pixel mapping of the frame a leaf belongs to.
+struct LView {
+    uint32_t *map;
+    PixelMap pm;
+    uint32_t n, max_dwell;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ LView leaf_view(const LeafArgs &a, uint32_t frame)
+{
+    LView v;
+    if (BATCH) {
+        const FrameDesc &d = a.frames[frame];
+        v.map = d.map;
+        v.pm = d.pm;
+        v.n = d.n;
+        v.max_dwell = d.max_dwell;
+    } else {
+        v.map = a.map;
+        v.pm = a.pm;
+        v.n = a.n;
+        v.max_dwell = a.max_dwell;
+    }
+    return v;
+}
+
 // Exact dwell of a parked orbit: state (x, y) after d updates, that state
 // known to pass the test, and "escaped, or d >= max_dwell" known to hold
 // kLeafUnroll updates later.  Points where escape is not absorbing take the
-// tested loop instead.
-template <bool COUNT>
-__device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2 u,
+// tested loop instead.  u = (count, py << 16 | px, frame).
+template <bool COUNT, bool BATCH>
+__device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint4 u,
                                               unsigned long long &it)
 {
+    const LView v = leaf_view<BATCH>(a, u.z);
     const uint32_t px = u.y & 0xffffu, py = u.y >> 16;
-    const float2 c = pixel_c(a.pm, px, py);
+    const float2 c = pixel_c(v.pm, px, py);
     uint32_t d = u.x;
     float x = s.x, y = s.y;
     if (!escape_absorbing(c.x, c.y)) {
-        while (d < a.max_dwell && z_bounded(x, y)) {
+        while (d < v.max_dwell && z_bounded(x, y)) {
             z_update(x, y, c.x, c.y);
             ++d;
         }
-    } else if (d < a.max_dwell) {
+    } else if (d < v.max_dwell) {
         // invariant: count d passes (d < max_dwell) and the predicate holds
         // at d + 2h; halve h until the first count where it holds is d + 1
 #pragma unroll
@@ -580,7 +682,7 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2
 #pragma unroll
             for (uint32_t k = 0; k < h; ++k)
                 z_update(tx, ty, c.x, c.y);
-            const bool hit = (a.max_dwell - d <= h) || !z_bounded(tx, ty);
+            const bool hit = (v.max_dwell - d <= h) || !z_bounded(tx, ty);
             if (!hit) {
                 x = tx;
                 y = ty;
@@ -589,7 +691,7 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint2
         }
         d += 1u;
     }
-    a.map[(size_t)py * a.n + px] = d;
+    v.map[(size_t)py * v.n + px] = d;
     if (COUNT)
         it += d;
 }
@@ -605,11 +707,12 @@ __device__ __forceinline__ uint32_t rows_in(uint32_t q, float inv_w)
 // One orbit slot of a lane.
 struct Slot {
     float x, y, cr, ci;
-    uint32_t d, pix;
+    uint32_t d, pix, md;  // count, pixel (py << 16 | px), max_dwell of its frame
     bool busy, fast;
 };
 
-__device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t px, uint32_t py)
+__device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t md, uint32_t px,
+                                           uint32_t py)
 {
     const float2 c = pixel_c(pm, px, py);
     o.cr = c.x;
@@ -618,35 +721,43 @@ __device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t
     o.y = 0.0f;
     o.d = 0;
     o.pix = (py << 16) | px;
+    o.md = md;
     o.fast = escape_absorbing(c.x, c.y);
     o.busy = true;
 }
 
 // Each lane carries two independent orbits, so one round's bookkeeping
 // (votes, refills, parking) serves two blocks of updates, and the two update
-// chains interleave.
-template <bool COUNT>
+// chains interleave.  All lanes of a warp work on the same leaf (the same
+// frame) at a time; parked orbits remember their frame.
+template <bool COUNT, bool BATCH>
 __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs a)
 {
+    using R = Rec<BATCH>;
+    using T = typename R::T;
     __shared__ float2 park_s[kRefillWarps][kParkCap];  // saved state
-    __shared__ uint2 park_u[kRefillWarps][kParkCap];   // count, pixel (py << 16 | px)
+    __shared__ uint4 park_u[kRefillWarps][kParkCap];   // count, pixel, frame
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     float2 *qs = park_s[wib];
-    uint2 *qu = park_u[wib];
+    uint4 *qu = park_u[wib];
     uint32_t parked = 0;  // warp-uniform
 
+    const T *leaves = static_cast<const T *>(a.leaves);
     const uint32_t nleaves = min(a.ctr->leaf_count, a.leaf_cap);
     const uint32_t K = (uint32_t)kLeafUnroll;
     // the warp's current leaf: the part still to hand out, as a row-major cursor
-    uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1;
+    uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1, frame = 0;
     float inv_cw = 1.0f;
+    LView lv = leaf_view<BATCH>(a, 0u);
     bool more = true;
     Slot s0, s1;
     s0.busy = s1.busy = false;
     s0.fast = s1.fast = false;
     s0.x = s0.y = s0.cr = s0.ci = s1.x = s1.y = s1.cr = s1.ci = 0.0f;
     s0.d = s1.d = s0.pix = s1.pix = 0;
+    s0.md = s1.md = 0;
+    uint32_t f0 = 0, f1 = 0;  // frames of the slots' orbits
     unsigned long long it = 0, lpx = 0;
 
     for (;;) {
@@ -662,7 +773,11 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                     more = false;
                     break;
                 }
-                const Region g = unpack_region(a.leaves[li]);
+                const T e = leaves[li];
+                const Region g = R::region(e);
+                frame = R::frame(e);
+                if (BATCH)
+                    lv = leaf_view<BATCH>(a, frame);
                 if (a.skip_perimeter) {
                     // only the interior; a leaf of side <= 2 is all perimeter
                     cw = g.w > 2u ? g.w - 2u : 1u;
@@ -685,11 +800,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             const uint32_t r1 = n0 + (uint32_t)__popc(i1 & lt_mask);
             if (!s0.busy && r0 < take) {
                 const uint32_t q = col0 + r0, dr = rows_in(q, inv_cw);
-                slot_start(s0, a.pm, ox + q - dr * cw, oy + row0 + dr);
+                slot_start(s0, lv.pm, lv.max_dwell, ox + q - dr * cw, oy + row0 + dr);
+                f0 = frame;
             }
             if (!s1.busy && r1 < take) {
                 const uint32_t q = col0 + r1, dr = rows_in(q, inv_cw);
-                slot_start(s1, a.pm, ox + q - dr * cw, oy + row0 + dr);
+                slot_start(s1, lv.pm, lv.max_dwell, ox + q - dr * cw, oy + row0 + dr);
+                f1 = frame;
             }
             {
                 const uint32_t q = col0 + take, dr = rows_in(q, inv_cw);
@@ -713,13 +830,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
         }
         bool park0 = false, park1 = false;
         if (s0.busy) {
-            if (s0.fast && a.max_dwell - s0.d >= K && z_bounded(s0.x, s0.y))
+            if (s0.fast && s0.md - s0.d >= K && z_bounded(s0.x, s0.y))
                 s0.d += K;
             else
                 park0 = true;  // escaped in this block, tail below max_dwell, or |c| near 2
         }
         if (s1.busy) {
-            if (s1.fast && a.max_dwell - s1.d >= K && z_bounded(s1.x, s1.y))
+            if (s1.fast && s1.md - s1.d >= K && z_bounded(s1.x, s1.y))
                 s1.d += K;
             else
                 park1 = true;
@@ -733,13 +850,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             if (park0) {
                 const uint32_t slot = parked + (uint32_t)__popc(p0 & lt_mask);
                 qs[slot] = make_float2(sx0, sy0);
-                qu[slot] = make_uint2(s0.d, s0.pix);
+                qu[slot] = make_uint4(s0.d, s0.pix, f0, 0u);
                 s0.busy = false;
             }
             if (park1) {
                 const uint32_t slot = parked + n0 + (uint32_t)__popc(p1 & lt_mask);
                 qs[slot] = make_float2(sx1, sy1);
-                qu[slot] = make_uint2(s1.d, s1.pix);
+                qu[slot] = make_uint4(s1.d, s1.pix, f1, 0u);
                 s1.busy = false;
             }
             parked += n0 + (uint32_t)__popc(p1);
@@ -747,9 +864,9 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             while (parked >= 32u) {
                 parked -= 32u;
                 const float2 sv = qs[parked + lane];
-                const uint2 uv = qu[parked + lane];
+                const uint4 uv = qu[parked + lane];
                 __syncwarp();
-                finish_parked<COUNT>(a, sv, uv, it);
+                finish_parked<COUNT, BATCH>(a, sv, uv, it);
                 if (COUNT)
                     ++lpx;
             }
@@ -757,7 +874,7 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
     }
     // ---- the orbits still parked
     if (lane < parked) {
-        finish_parked<COUNT>(a, qs[lane], qu[lane], it);
+        finish_parked<COUNT, BATCH>(a, qs[lane], qu[lane], it);
         if (COUNT)
             ++lpx;
     }
@@ -772,6 +889,32 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             if (lpx)
                 atomicAdd(&a.ctr->leaf_pixels, lpx);
         }
+    }
+}
+
+// Level-0 records and counters of a batch: block f writes frame f's
+// axis0 x axis0 initial regions at its offset; block 0 zeroes the counters.
+__global__ void init_batch_kernel(uint4 *__restrict__ olt0, uint4 *__restrict__ rst0,
+                                  DevCounters *ctr, const FrameDesc *frames, uint32_t total0)
+{
+    const uint32_t f = blockIdx.x;
+    if (f == 0) {
+        uint32_t *w = reinterpret_cast<uint32_t *>(ctr);
+        const uint32_t words = (uint32_t)(sizeof(DevCounters) / sizeof(uint32_t));
+        const uint32_t err_word = (uint32_t)(offsetof(DevCounters, error) / sizeof(uint32_t));
+        for (uint32_t k = threadIdx.x; k < words; k += blockDim.x)
+            if (k != err_word)
+                w[k] = (k == 0u) ? total0 : 0u;  // word 0 is count[0]
+    }
+    const FrameDesc &d = frames[f];
+    const uint32_t per = d.axis0 * d.axis0;
+    for (uint32_t k = threadIdx.x; k < per; k += blockDim.x) {
+        const uint32_t gx = k % d.axis0, gy = k / d.axis0;
+        const uint32_t x0 = gx * d.s0, y0 = gy * d.s0;
+        const uint2 rec = pack_region(x0, y0, min(d.s0, d.n - x0), min(d.s0, d.n - y0));
+        olt0[d.olt0_offset + k] = make_uint4(rec.x, rec.y, f, 0u);
+        if (rst0 != nullptr)
+            rst0[d.olt0_offset + k] = make_uint4(kNone, 0u, 0u, 0u);
     }
 }
 
@@ -816,38 +959,74 @@ cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_level(const LevelArgs &a, bool count, int sms, cudaStream_t s)
+template <bool COUNT, bool BATCH>
+static void level_launch(const LevelArgs &a, int sms, cudaStream_t s)
 {
     const size_t smem = (size_t)(256 / 32) * kWarpStage * sizeof(uint32_t);
-    if (count) {
-        const int grid = persistent_grid(level_kernel<true>, 256, smem, sms);
-        level_kernel<true><<<grid, 256, smem, s>>>(a);
+    const int grid = persistent_grid(level_kernel<COUNT, BATCH>, 256, smem, sms);
+    level_kernel<COUNT, BATCH><<<grid, 256, smem, s>>>(a);
+}
+
+cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cudaStream_t s)
+{
+    if (batch) {
+        if (count)
+            level_launch<true, true>(a, sms, s);
+        else
+            level_launch<false, true>(a, sms, s);
     } else {
-        const int grid = persistent_grid(level_kernel<false>, 256, smem, sms);
-        level_kernel<false><<<grid, 256, smem, s>>>(a);
+        if (count)
+            level_launch<true, false>(a, sms, s);
+        else
+            level_launch<false, false>(a, sms, s);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const FillArgs &f, int sms, cudaStream_t s)
+cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, cudaStream_t s)
 {
-    const int grid = persistent_grid(fill_kernel, 256, 0, sms);
-    fill_kernel<<<grid, 256, 0, s>>>(f);
+    if (batch) {
+        const int grid = persistent_grid(fill_kernel<true>, 256, 0, sms);
+        fill_kernel<true><<<grid, 256, 0, s>>>(f);
+    } else {
+        const int grid = persistent_grid(fill_kernel<false>, 256, 0, sms);
+        fill_kernel<false><<<grid, 256, 0, s>>>(f);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, bool tiled,
-                        int sms, cudaStream_t s)
+cudaError_t launch_init_batch(uint4 *olt0, uint4 *rst0, DevCounters *ctr, const FrameDesc *frames,
+                              uint32_t nframes, uint32_t total0, cudaStream_t s)
 {
+    init_batch_kernel<<<nframes, 256, 0, s>>>(olt0, rst0, ctr, frames, total0);
+    return cudaGetLastError();
+}
+
+template <bool COUNT, bool BATCH>
+static void refill_launch(const LeafArgs &a, int sms, cudaStream_t s)
+{
+    const int threads = kRefillWarps * 32;
+    const int grid = persistent_grid(leaf_refill_kernel<COUNT, BATCH>, threads, 0, sms);
+    leaf_refill_kernel<COUNT, BATCH><<<grid, threads, 0, s>>>(a);
+}
+
+cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, bool tiled,
+                        bool batch, int sms, cudaStream_t s)
+{
+    if (batch) {
+        if (tiled)
+            return cudaErrorInvalidValue;
+        if (count)
+            refill_launch<true, true>(a, sms, s);
+        else
+            refill_launch<false, true>(a, sms, s);
+        return cudaGetLastError();
+    }
     if (!tiled) {
-        const int threads = kRefillWarps * 32;
-        if (count) {
-            const int grid = persistent_grid(leaf_refill_kernel<true>, threads, 0, sms);
-            leaf_refill_kernel<true><<<grid, threads, 0, s>>>(a);
-        } else {
-            const int grid = persistent_grid(leaf_refill_kernel<false>, threads, 0, sms);
-            leaf_refill_kernel<false><<<grid, threads, 0, s>>>(a);
-        }
+        if (count)
+            refill_launch<true, false>(a, sms, s);
+        else
+            refill_launch<false, false>(a, sms, s);
         return cudaGetLastError();
     }
     const uint32_t tiles_x = (a.side + bx - 1) / bx, tiles_y = (a.side + by - 1) / by;

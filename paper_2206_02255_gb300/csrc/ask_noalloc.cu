@@ -229,7 +229,7 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
         a.fill_cap = 0u;
         a.exact_last = 0u;
         a.ctr = sc->ctr;
-        if (launch_level(a, false, sc->sms, s) != cudaSuccess)
+        if (launch_level(a, false, false, sc->sms, s) != cudaSuccess)
             return ASK_ECUDA;
     }
     LeafArgs la;
@@ -242,7 +242,7 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
     la.leaf_cap = kNoAllocRegions;
     la.skip_perimeter = 0u;
     la.ctr = sc->ctr;
-    if (launch_leaf(la, p.block_x, p.block_y, false, false, sc->sms, s) != cudaSuccess)
+    if (launch_leaf(la, p.block_x, p.block_y, false, false, false, sc->sms, s) != cudaSuccess)
         return ASK_ECUDA;
     return ASK_OK;
 }

@@ -62,3 +62,75 @@ def random_windows(k, seed, span=(1e-3, 3.0)):
         im0 = rng.uniform(-1.6, 1.6 - wi) if wi < 3.2 else -1.6
         out.append((re0, re0 + wr, im0, im0 + wi))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Batched and served workloads: frames zoomed on points of the set's boundary.
+# The candidate centres are boundary pixels of the n = 1024, dwell 512 map
+# (a pixel below the cap next to one at the cap), written once by
+# tests/golden/make_boundary_centers.py from the CPU reference.
+# ---------------------------------------------------------------------------
+import math
+import os
+
+BOUNDARY_CENTERS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "tests", "golden", "boundary_centers.tsv")
+
+
+def boundary_centers():
+    """[(cr, ci)] of the stored boundary pixels."""
+    out = []
+    with open(BOUNDARY_CENTERS) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            cols = line.split("\t")
+            out.append((float(cols[2]), float(cols[3])))
+    return out
+
+
+def _log_uniform(rng, lo, hi):
+    return math.exp(rng.uniform(math.log(lo), math.log(hi)))
+
+
+def _zoom_window(center, zoom):
+    # zoom 1 is the 2 x 2 window of the n = 1024 configuration
+    hw = 1.0 / zoom
+    cr, ci = center
+    return (cr - hw, cr + hw, ci - hw, ci + hw)
+
+
+def batch_frames(count=256, seed=0, sides=(512, 8192), zooms=(1.0, 1e4), dwells=(256, 8192)):
+    """Frames of the batched workload: side uniform in `sides`, centre drawn
+    from the boundary centres, zoom log-uniform in `zooms`, dwell cap a
+    log-uniform integer in `dwells`.  Returns dicts with window, n,
+    max_dwell, zoom."""
+    rng = random.Random(seed)
+    centers = boundary_centers()
+    out = []
+    for _ in range(count):
+        n = rng.randint(*sides)
+        c = rng.choice(centers)
+        zoom = _log_uniform(rng, *zooms)
+        md = int(round(_log_uniform(rng, *dwells)))
+        out.append(dict(window=_zoom_window(c, zoom), n=n, max_dwell=md, zoom=zoom))
+    return out
+
+
+def serving_requests(count=2000, seed=7, rate=200.0, sides=(256, 4096), zooms=(1.0, 1e4),
+                     dwells=(512, 4096)):
+    """Requests of the served workload: Poisson arrivals at `rate` per second
+    (seconds from 0 in `t`), side uniform in `sides`, centre and zoom as in
+    batch_frames, dwell cap uniform in `dwells`."""
+    rng = random.Random(seed)
+    centers = boundary_centers()
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += rng.expovariate(rate)
+        n = rng.randint(*sides)
+        c = rng.choice(centers)
+        zoom = _log_uniform(rng, *zooms)
+        md = rng.randint(*dwells)
+        out.append(dict(id=k, t=t, window=_zoom_window(c, zoom), n=n, max_dwell=md, zoom=zoom))
+    return out

@@ -1,0 +1,102 @@
+"""Batched renders (many frames, one launch chain) and their CUDA-graph
+form, through the C ABI, against the CPU reference frame by frame."""
+import numpy as np
+import pytest
+
+from paper_2206_02255_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _frames(asklib, specs):
+    import torch
+    out = []
+    for win, n, M, g, r, B in specs:
+        out.append(dict(window=win, n=n, max_dwell=M, g=g, r=r, B=B,
+                        out=torch.full((n, n), -1, dtype=torch.int32, device="cuda")))
+    return out
+
+
+def _map(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+MIXED = [
+    (inputs.WINDOW_PAPER, 1024, 512, 16, 2, 32),
+    (inputs.WINDOW_WIDE, 97, 200, 3, 2, 4),
+    ((-0.8, -0.6, 0.05, 0.30), 513, 700, 7, 4, 8),
+    ((-2.0, 0.47, -1.12, 1.12), 256, 64, 4, 8, 2),
+    (inputs.WINDOW_PAPER, 2048, 2048, 32, 4, 16),
+    ((-1.9, 0.6, -0.3, 1.2), 1000, 1, 5, 3, 16),
+    ((0.25, 0.26, -0.005, 0.005), 777, 3000, 2, 2, 8),
+]
+
+
+@pytest.mark.parametrize("exact", [False, True], ids=["query", "exact_borders"])
+def test_batch_matches_oracle(ctx, orc, asklib, exact):
+    import torch
+    frames = _frames(asklib, MIXED)
+    flags = asklib.FLAG_COUNT | (asklib.FLAG_EXACT_BORDERS if exact else 0)
+    st = ctx.render_batch(frames, flags=flags, stats=True)
+    torch.cuda.synchronize()
+    regions = {}
+    leaves = 0
+    for f, (win, n, M, g, r, B) in zip(frames, MIXED):
+        want, ost = orc.render_ms(win, n, M, g, r, B)
+        got = _map(f["out"])
+        assert np.array_equal(got, want), (n, g, r, B, int((got != want).sum()))
+        for i, v in enumerate(ost["regions_per_level"]):
+            regions[i] = regions.get(i, 0) + v
+        leaves += ost["leaves"]
+    assert st["regions_per_level"] == [regions[i] for i in range(len(regions))]
+    assert st["leaves"] == leaves
+
+
+def test_batch_single_frame_and_graph(ctx, orc, asklib):
+    """Zoomed boundary frames of the batched workload (sides scaled down):
+    each render alone, the batch, and two replays of its graph agree."""
+    import torch
+    specs = []
+    for k, f in enumerate(inputs.batch_frames(count=10, seed=3, sides=(300, 1500),
+                                              dwells=(256, 4096))):
+        specs.append((f["window"], f["n"], f["max_dwell"], [8, 16, 32][k % 3], [2, 4][k % 2], 16))
+    frames = _frames(asklib, specs)
+    alone = []
+    for win, n, M, g, r, B in specs:
+        o = ctx.render("ask", win, n, M, asklib.make_params(g, r, B))
+        alone.append(_map(o))
+    ctx.render_batch(frames)
+    torch.cuda.synchronize()
+    for f, a in zip(frames, alone):
+        assert np.array_equal(_map(f["out"]), a)
+    graph = ctx.graph_batch(frames)
+    for _ in range(2):
+        for f in frames:
+            f["out"].fill_(-1)
+        graph.launch()
+        torch.cuda.synchronize()
+        for f, a in zip(frames, alone):
+            assert np.array_equal(_map(f["out"]), a)
+    graph.close()
+    # spot-check two frames against the reference
+    for k in (0, 7):
+        win, n, M, g, r, B = specs[k]
+        want, _ = orc.render_ms(win, n, M, g, r, B)
+        assert np.array_equal(alone[k], want)
+
+
+def test_batch_argument_errors(ctx, asklib):
+    import torch
+    frames = _frames(asklib, MIXED[:4])
+    frames[2]["r"] = 1
+    with pytest.raises(asklib.AskError) as e:
+        ctx.render_batch(frames)
+    assert e.value.status == asklib.EINVAL and "frame 2" in str(e.value)
+    frames[2]["r"] = 2
+    with pytest.raises(asklib.AskError):
+        ctx.render_batch(frames, flags=asklib.FLAG_TIMING)
+    with pytest.raises(asklib.AskError):
+        ctx.graph_batch(frames, flags=asklib.FLAG_COUNT)
+    with pytest.raises(asklib.AskError):
+        ctx.render_batch([])
+    torch.cuda.synchronize()
