@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--max-dwell", type=int, default=None)
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the exhaustive and CDP2 comparison arms")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: one n=16384 map per step (default); batch: 256 frames of "
+                         "mixed size and zoom per step; serve: Poisson render requests")
+    ap.add_argument("--frames", type=int, default=256, help="batch: frames per step")
     return ap.parse_args()
 
 
@@ -421,10 +425,125 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: 256 frames, sides 512..8192, zoomed on boundary points
+# ---------------------------------------------------------------------------
+def run_batch(args):
+    import torch
+
+    from paper_2206_02255_gb300 import ask, autotune, build, costmodel, inputs
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    ctx = ask.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    frames = inputs.batch_frames(count=args.frames, seed=0 + rank)
+    sizes = [f["n"] * f["n"] for f in frames]
+    pad = [(z + 3) // 4 * 4 for z in sizes]               # keep every map 16-byte aligned
+    total_px = float(sum(sizes))
+    big = torch.empty(sum(pad), dtype=torch.int32, device=dev)
+    off = 0
+    for f, z, zp in zip(frames, sizes, pad):
+        f["out"] = big[off:off + z].view(f["n"], f["n"])
+        off += zp
+
+    tuner = autotune.BatchTuner(ctx, probes=6).fit(frames)
+    for f in frames:
+        f["g"], f["r"], f["B"] = tuner.choose(f)
+    probe_models = []
+    for pf, cfg, _ in tuner.probes:
+        mc = autotune.model_choice(ctx, pf["window"], pf["n"], pf["max_dwell"], cfg["g"], cfg["r"],
+                                   cfg["B"])
+        probe_models.append(dict(n=pf["n"], max_dwell=pf["max_dwell"],
+                                 measured=(cfg["g"], cfg["r"], cfg["B"]),
+                                 model=(mc["g"], mc["r"], mc["B"]), P=round(mc["P"], 3)))
+
+    def per_frame():
+        for f in frames:
+            ctx.render("ask", f["window"], f["n"], f["max_dwell"],
+                       ask.make_params(f["g"], f["r"], f["B"]), out=f["out"])
+
+    def batched():
+        ctx.render_batch(frames)
+
+    graph = ctx.graph_batch(frames)
+
+    def timed(fn, steps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(world, e0.elapsed_time(e1) / steps, dev)
+
+    clocks = ClockSampler(local)
+    ms_frame = timed(per_frame, args.steps)
+    clocks.start()
+    time.sleep(0.3)
+    ms_batch = timed(batched, args.steps)
+    clk = clocks.stop()
+    ms_graph = timed(graph.launch, args.steps)
+    _, st = None, ctx.render_batch(frames, flags=ask.FLAG_COUNT, stats=True)
+    launches = st["kernel_launches"]
+
+    # end to end: the batched render plus every map copied to pinned host memory
+    host = torch.empty(sum(pad), dtype=torch.int32, pin_memory=True)
+    steps_e2e = max(2, args.steps // 2)
+    batched()
+    host.copy_(big, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps_e2e):
+        batched()
+        host.copy_(big, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / steps_e2e, dev)
+    graph.close()
+
+    if rank == 0:
+        gp = lambda ms: world * total_px / (ms / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": gp(ms_batch), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch_%d_frames_side512-8192_zoom1-1e4_dwell256-8192" % len(frames),
+                       "frames": len(frames), "pixels": int(total_px), "method": "ask_batch",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "%.1f GB of maps per step > 129 MB L2" % (4 * total_px / 1e9)},
+            "per_frame_ask": {"ms": ms_frame, "gpix_s": gp(ms_frame)},
+            "batched": {"ms": ms_batch, "gpix_s": gp(ms_batch), "launches": launches},
+            "graph": {"ms": ms_graph, "gpix_s": gp(ms_graph)},
+            "speedup_batch_vs_per_frame": ms_frame / ms_batch,
+            "dwell_iter_s": {"executed": st["iterations"] / (ms_batch / 1e3)},
+            "tuned_probes": tuner.summary(), "model_vs_measured": probe_models,
+            "e2e": {"value": gp(t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(4 * total_px), "ms_per_step": 1e3 * t_e2e},
+            "gpu_launches": launches * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve(args):
+    raise SystemExit("--workload serve: see paper_2206_02255_gb300/serve.py")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 
