@@ -532,8 +532,69 @@ def run_batch(args):
     ctx.close()
 
 
+# ---------------------------------------------------------------------------
+# Served workload: Poisson render requests, continuous batching
+# ---------------------------------------------------------------------------
 def run_serve(args):
-    raise SystemExit("--workload serve: see paper_2206_02255_gb300/serve.py")
+    import torch
+
+    from paper_2206_02255_gb300 import ask, autotune, build, inputs, serve
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    ctx = ask.Context(local)
+    reqs = inputs.serving_requests(count=2000, seed=7 + rank)
+    tuner = autotune.BatchTuner(ctx, probes=4).fit(reqs[::20])
+    cfg = {d["id"]: tuner.choose(d) for d in reqs}
+
+    def fresh(ds, at_zero=False):
+        out = []
+        for d in ds:
+            q = serve.Request(d, *cfg[d["id"]])
+            if at_zero:
+                q.t = 0.0
+            out.append(q)
+        return out
+
+    # warm up both paths (allocator caches, first launches)
+    srv = serve.Server(device=local, slots=2, budget_bytes=40 * 2 ** 30)
+    srv.run(fresh(reqs[:32], at_zero=True))
+    serve.serve_per_frame(ctx, fresh(reqs[:8], at_zero=True))
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    served = serve.summarize(srv.run(fresh(reqs)))
+    clk = clocks.stop()
+    alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs)))
+    # saturation: the first 600 requests all waiting at t = 0
+    sat_served = serve.summarize(srv.run(fresh(reqs[:600], at_zero=True)))
+    sat_alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs[:600], at_zero=True)))
+    srv.close()
+    px = float(sum(d["n"] * d["n"] for d in reqs))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": served["gpix_s"] * world, "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * served["span_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serve_2000_poisson200_side256-4096_dwell512-4096",
+                       "requests": len(reqs), "rate_per_s": 200, "budget_gb": 40, "slots": 2,
+                       "pixels": int(px), "method": "ask_batch continuous batching"},
+            "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"], "max": served["max_ms"]},
+            "per_frame_ask": {"p50_ms": alone["p50_ms"], "p99_ms": alone["p99_ms"],
+                              "gpix_s": alone["gpix_s"]},
+            "saturated_600": {"served_gpix_s": sat_served["gpix_s"],
+                              "per_frame_gpix_s": sat_alone["gpix_s"],
+                              "served_p99_ms": sat_served["p99_ms"],
+                              "per_frame_p99_ms": sat_alone["p99_ms"]},
+            "e2e": {"value": served["gpix_s"] * world, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(4 * px), "note": "latency includes the D2H copy"},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def main():

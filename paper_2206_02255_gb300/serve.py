@@ -1,0 +1,155 @@
+"""Render server with continuous batching.
+
+Requests (window, n, dwell cap) arrive over time.  The server keeps a queue
+of arrived requests and a fixed number of batch slots, each a context (its
+own region tables on the device) with its own CUDA stream.  Whenever a slot
+is free it admits queued requests, oldest first, while their dwell buffers
+fit in the memory budget, and renders them as one batch (one launch chain
+for every frame of the batch, region queues on the device); the maps are
+then copied to pinned host memory on the same stream.  Requests that arrive
+while batches run wait for the next free slot, so the work of consecutive
+batches overlaps on the device.  A request's latency runs from its arrival
+to the moment its map is in host memory.
+
+The baseline, :func:`serve_per_frame`, renders the same requests one at a
+time, in arrival order, with the single-frame ASK call.
+"""
+import time
+
+from . import ask
+
+
+class Request:
+    __slots__ = ("id", "t", "window", "n", "max_dwell", "g", "r", "B", "out", "host",
+                 "t_done", "event")
+
+    def __init__(self, d, g, r, B):
+        self.id = d["id"]
+        self.t = d["t"]
+        self.window = d["window"]
+        self.n = d["n"]
+        self.max_dwell = d["max_dwell"]
+        self.g, self.r, self.B = g, r, B
+        self.out = self.host = self.event = None
+        self.t_done = None
+
+    @property
+    def nbytes(self):
+        return 4 * self.n * self.n
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return float("nan")
+    k = (len(xs) - 1) * q / 100.0
+    lo, hi = int(k), min(int(k) + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+class Server:
+    """Continuous-batching server over `slots` contexts on one device."""
+
+    def __init__(self, device=0, slots=2, budget_bytes=40 * 2 ** 30, max_frames=256):
+        import torch
+        self.device = device
+        self.budget = budget_bytes
+        self.max_frames = max_frames
+        self.ctxs = [ask.Context(device) for _ in range(slots)]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self.busy = [None] * slots       # list of requests in flight per slot
+        self.used = 0                    # bytes of dwell buffers in flight
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+    def _start(self, slot, reqs):
+        import torch
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            for q in reqs:
+                q.out = torch.empty((q.n, q.n), dtype=torch.int32, device="cuda:%d" % self.device)
+                q.host = torch.empty((q.n, q.n), dtype=torch.int32, pin_memory=True)
+            frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r, B=q.B,
+                           out=q.out) for q in reqs]
+            self.ctxs[slot].render_batch(frames, stream=s)
+            for q in reqs:
+                q.host.copy_(q.out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        for q in reqs:
+            q.event = ev
+        self.busy[slot] = reqs
+
+    def run(self, requests, poll_s=0.0002):
+        """Serve `requests` (sorted by arrival time t, seconds from start) in
+        real time; returns them with t_done set (seconds from start)."""
+        pending = []
+        k = 0
+        t0 = time.perf_counter()
+        done = 0
+        while done < len(requests):
+            now = time.perf_counter() - t0
+            while k < len(requests) and requests[k].t <= now:
+                pending.append(requests[k])
+                k += 1
+            # retire finished batches
+            for slot, reqs in enumerate(self.busy):
+                if reqs is not None and reqs[0].event.query():
+                    tn = time.perf_counter() - t0
+                    for q in reqs:
+                        q.t_done = tn
+                        self.used -= q.nbytes
+                        q.out = None
+                    done += len(reqs)
+                    self.busy[slot] = None
+            # admit queued requests into free slots while they fit the budget
+            for slot in range(len(self.ctxs)):
+                if self.busy[slot] is not None or not pending:
+                    continue
+                take, mem = [], 0
+                while pending and len(take) < self.max_frames and \
+                        self.used + mem + pending[0].nbytes <= self.budget:
+                    mem += pending[0].nbytes
+                    take.append(pending.pop(0))
+                if take:
+                    self.used += mem
+                    self._start(slot, take)
+            if k < len(requests) and not pending and all(b is None for b in self.busy):
+                # idle until the next arrival
+                wait = requests[k].t - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+            else:
+                time.sleep(poll_s)
+        return requests
+
+
+def serve_per_frame(ctx, requests, poll_s=0.0002):
+    """Baseline: one request at a time in arrival order, single-frame ASK,
+    map copied to pinned host memory; returns requests with t_done set."""
+    import torch
+    s = torch.cuda.Stream(device=ctx.device)
+    t0 = time.perf_counter()
+    for q in requests:
+        while time.perf_counter() - t0 < q.t:
+            time.sleep(poll_s)
+        with torch.cuda.stream(s):
+            q.out = torch.empty((q.n, q.n), dtype=torch.int32, device="cuda:%d" % ctx.device)
+            q.host = torch.empty((q.n, q.n), dtype=torch.int32, pin_memory=True)
+            ctx.render("ask", q.window, q.n, q.max_dwell, ask.make_params(q.g, q.r, q.B),
+                       out=q.out, stream=s)
+            q.host.copy_(q.out, non_blocking=True)
+        s.synchronize()
+        q.t_done = time.perf_counter() - t0
+        q.out = None
+    return requests
+
+
+def summarize(requests):
+    lat = [1e3 * (q.t_done - q.t) for q in requests]
+    px = sum(q.n * q.n for q in requests)
+    span = max(q.t_done for q in requests) - min(q.t for q in requests)
+    return dict(requests=len(requests), p50_ms=percentile(lat, 50), p99_ms=percentile(lat, 99),
+                max_ms=max(lat), gpix_s=px / span / 1e9, span_s=span)
