@@ -558,19 +558,22 @@ def run_serve(args):
             out.append(q)
         return out
 
-    # warm up both paths (allocator caches, first launches)
-    srv = serve.Server(device=local, slots=2, budget_bytes=40 * 2 ** 30)
-    srv.run(fresh(reqs[:32], at_zero=True))
-    serve.serve_per_frame(ctx, fresh(reqs[:8], at_zero=True))
+    # both paths share one pinned-buffer pool; results are released when
+    # delivered.  Warm up (allocator caches, pinned buffers, first launches).
+    pool = serve.PinnedPool()
+    srv = serve.Server(device=local, slots=2, budget_bytes=40 * 2 ** 30, pool=pool, keep=False)
+    srv.run(fresh(reqs[:64], at_zero=True))
+    serve.serve_per_frame(ctx, fresh(reqs[:64], at_zero=True), pool=pool, keep=False)
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
     served = serve.summarize(srv.run(fresh(reqs)))
     clk = clocks.stop()
-    alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs)))
+    alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs), pool=pool, keep=False))
     # saturation: the first 600 requests all waiting at t = 0
     sat_served = serve.summarize(srv.run(fresh(reqs[:600], at_zero=True)))
-    sat_alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs[:600], at_zero=True)))
+    sat_alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs[:600], at_zero=True), pool=pool,
+                                                      keep=False))
     srv.close()
     px = float(sum(d["n"] * d["n"] for d in reqs))
     if rank == 0:

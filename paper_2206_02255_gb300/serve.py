@@ -19,9 +19,29 @@ import time
 from . import ask
 
 
+class PinnedPool:
+    """Pinned host buffers by power-of-two size class, reused across
+    requests: pinning memory is slow, so a served path allocates once and
+    recycles (a buffer goes back when its request's result is consumed)."""
+
+    def __init__(self):
+        self.free = {}
+
+    def get(self, n):
+        import torch
+        nbytes = 4 * n * n
+        cls = 1 << max(12, (nbytes - 1).bit_length())
+        lst = self.free.get(cls)
+        buf = lst.pop() if lst else torch.empty(cls, dtype=torch.uint8, pin_memory=True)
+        return buf, buf[:nbytes].view(torch.int32).view(n, n)
+
+    def put(self, buf):
+        self.free.setdefault(buf.numel(), []).append(buf)
+
+
 class Request:
     __slots__ = ("id", "t", "window", "n", "max_dwell", "g", "r", "B", "out", "host",
-                 "t_done", "event")
+                 "hbuf", "t_done", "event")
 
     def __init__(self, d, g, r, B):
         self.id = d["id"]
@@ -30,7 +50,7 @@ class Request:
         self.n = d["n"]
         self.max_dwell = d["max_dwell"]
         self.g, self.r, self.B = g, r, B
-        self.out = self.host = self.event = None
+        self.out = self.host = self.hbuf = self.event = None
         self.t_done = None
 
     @property
@@ -50,9 +70,12 @@ def percentile(xs, q):
 class Server:
     """Continuous-batching server over `slots` contexts on one device."""
 
-    def __init__(self, device=0, slots=2, budget_bytes=40 * 2 ** 30, max_frames=256):
+    def __init__(self, device=0, slots=2, budget_bytes=40 * 2 ** 30, max_frames=256, pool=None,
+                 keep=True):
         import torch
         self.device = device
+        self.pool = pool if pool is not None else PinnedPool()
+        self.keep = keep  # keep results on the requests; else recycle at completion
         self.budget = budget_bytes
         self.max_frames = max_frames
         self.ctxs = [ask.Context(device) for _ in range(slots)]
@@ -70,7 +93,7 @@ class Server:
         with torch.cuda.stream(s):
             for q in reqs:
                 q.out = torch.empty((q.n, q.n), dtype=torch.int32, device="cuda:%d" % self.device)
-                q.host = torch.empty((q.n, q.n), dtype=torch.int32, pin_memory=True)
+                q.hbuf, q.host = self.pool.get(q.n)
             frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r, B=q.B,
                            out=q.out) for q in reqs]
             self.ctxs[slot].render_batch(frames, stream=s)
@@ -102,6 +125,9 @@ class Server:
                         q.t_done = tn
                         self.used -= q.nbytes
                         q.out = None
+                        if not self.keep:
+                            self.pool.put(q.hbuf)
+                            q.hbuf = q.host = None
                     done += len(reqs)
                     self.busy[slot] = None
             # admit queued requests into free slots while they fit the budget
@@ -126,10 +152,11 @@ class Server:
         return requests
 
 
-def serve_per_frame(ctx, requests, poll_s=0.0002):
+def serve_per_frame(ctx, requests, poll_s=0.0002, pool=None, keep=True):
     """Baseline: one request at a time in arrival order, single-frame ASK,
     map copied to pinned host memory; returns requests with t_done set."""
     import torch
+    pool = pool if pool is not None else PinnedPool()
     s = torch.cuda.Stream(device=ctx.device)
     t0 = time.perf_counter()
     for q in requests:
@@ -137,13 +164,16 @@ def serve_per_frame(ctx, requests, poll_s=0.0002):
             time.sleep(poll_s)
         with torch.cuda.stream(s):
             q.out = torch.empty((q.n, q.n), dtype=torch.int32, device="cuda:%d" % ctx.device)
-            q.host = torch.empty((q.n, q.n), dtype=torch.int32, pin_memory=True)
+            q.hbuf, q.host = pool.get(q.n)
             ctx.render("ask", q.window, q.n, q.max_dwell, ask.make_params(q.g, q.r, q.B),
                        out=q.out, stream=s)
             q.host.copy_(q.out, non_blocking=True)
         s.synchronize()
         q.t_done = time.perf_counter() - t0
         q.out = None
+        if not keep:
+            pool.put(q.hbuf)
+            q.hbuf = q.host = None
     return requests
 
 
