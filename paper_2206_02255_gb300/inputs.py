@@ -11,6 +11,8 @@ shape (Sec. 6.2, Table 2, Fig. 6).  The configurations below follow that
 recipe at three sizes.
 """
 import itertools
+import math
+import os
 import random
 
 # Window corners as (re_min, re_max, im_min, im_max).  The paper's
@@ -70,9 +72,6 @@ def random_windows(k, seed, span=(1e-3, 3.0)):
 # (a pixel below the cap next to one at the cap), written once by
 # tests/golden/make_boundary_centers.py from the CPU reference.
 # ---------------------------------------------------------------------------
-import math
-import os
-
 BOUNDARY_CENTERS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                                 "tests", "golden", "boundary_centers.tsv")
 
