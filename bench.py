@@ -349,6 +349,50 @@ def run_gpu(args):
         cg, cr, cB, cblk = cdp_cfg[:4]
         ms_cdp_fnf = time_renders("cdp2", cg, cr, cB, cblk, reps, fnf)
         ms_cdp = time_renders("cdp2", cg, cr, cB, cblk, 1)
+    # ---- the paper's SBR / MBR mappings (Sec. 4.3), each tuned on its own
+    schemes = None
+    if not args.no_compare:
+        reps = max(3, args.steps // 4)
+        schemes = {"ask_default": {"ms": ms_step, "g": g, "r": r, "B": B, "block": list(blk)}}
+        space = [(sg, sr, sB, sblk) for sg in (8, 16, 32, 64) for sr in (2, 4)
+                 for sB in (16, 32, 64) for sblk in ((16, 16), (32, 8))]
+        fnf = ask.FLAG_CDP2_FIRE_AND_FORGET
+        for name, method, f in (("ask_sbr", "ask", ask.FLAG_SBR), ("ask_mbr", "ask", ask.FLAG_MBR),
+                                ("dp_mbr", "cdp2", ask.FLAG_MBR | fnf)):
+            bestc = None
+            for sg, sr, sB, sblk in space:
+                t = time_renders(method, sg, sr, sB, sblk, 1, f)
+                if bestc is None or t < bestc[4]:
+                    bestc = (sg, sr, sB, sblk, t)
+            sg, sr, sB, sblk = bestc[:4]
+            schemes[name] = {"ms": time_renders(method, sg, sr, sB, sblk, reps, f),
+                             "g": sg, "r": sr, "B": sB, "block": list(sblk)}
+            if method == "cdp2":
+                schemes[name]["fire_and_forget"] = True
+                schemes[name]["ms_tail_launch"] = time_renders(method, sg, sr, sB, sblk, 1,
+                                                               ask.FLAG_MBR)
+        if cdp_cfg is not None:
+            schemes["dp_sbr"] = {"ms": ms_cdp_fnf, "ms_tail_launch": ms_cdp, "fire_and_forget": True,
+                                 "g": cdp_cfg[0], "r": cdp_cfg[1], "B": cdp_cfg[2],
+                                 "block": list(cdp_cfg[3])}
+
+    # ---- cost model (Sec. 4) beside the tuner and the paper's configurations
+    model = None
+    if not args.no_compare:
+        from paper_2206_02255_gb300 import autotune
+        mc = autotune.model_choice(ctx, win, n, M, g, r, B)
+        model = {"P": mc["P"], "lambda_fit": mc["lam"], "kappa_ms": mc["kappa_ms"],
+                 "q": mc["q"], "c": mc["c"], "model_speedup_vs_ex": mc["model_speedup"],
+                 "model_optimum": [mc["g"], mc["r"], mc["B"]], "tuned": [g, r, B],
+                 "tuned_ms": ms_step}
+        try:
+            model["model_optimum_ms"] = time_renders("ask", mc["g"], mc["r"], mc["B"], blk, 3)
+        except ask.AskError as exc:
+            model["model_optimum_ms"] = None
+            model["model_optimum_error"] = str(exc)
+        model["paper_configs_ms"] = {"%d,%d,%d" % pc: time_renders("ask", *pc, blk, 3)
+                                     for pc in ((32, 4, 16), (64, 4, 16))}
+
     pixels = float(n) * n
     value = world * pixels / (ms_step / 1e3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -424,6 +468,7 @@ def run_gpu(args):
             "speedup_vs_exhaustive": ms_ex / ms_step,
             "speedup_vs_cdp2": min(ms_cdp, ms_cdp_fnf) / ms_step,
             "mismatch_vs_exhaustive_pixels": mismatch,
+            "schemes": schemes, "cost_model": model,
             "kernels_ms": kern, "levels": cst["levels"],
             "regions_per_level": cst["regions_per_level"], "leaves": cst["leaves"],
             "fills_per_level": cst["fills_per_level"],
@@ -472,9 +517,18 @@ def run_batch(args):
     for pf, cfg, _ in tuner.probes:
         mc = autotune.model_choice(ctx, pf["window"], pf["n"], pf["max_dwell"], cfg["g"], cfg["r"],
                                    cfg["B"])
+        try:
+            scratch = torch.empty((pf["n"], pf["n"]), dtype=torch.int32, device=dev)
+            model_ms = autotune.time_config(ctx, pf["window"], pf["n"], pf["max_dwell"], mc["g"],
+                                            mc["r"], mc["B"], scratch)
+            del scratch
+        except ask.AskError:
+            model_ms = None
         probe_models.append(dict(n=pf["n"], max_dwell=pf["max_dwell"],
-                                 measured=(cfg["g"], cfg["r"], cfg["B"]),
-                                 model=(mc["g"], mc["r"], mc["B"]), P=round(mc["P"], 3)))
+                                 measured=(cfg["g"], cfg["r"], cfg["B"]), measured_ms=round(cfg["ms"], 3),
+                                 model=(mc["g"], mc["r"], mc["B"]),
+                                 model_ms=None if model_ms is None else round(model_ms, 3),
+                                 P=round(mc["P"], 3), lambda_fit=round(mc["lam"], 2)))
 
     def per_frame():
         for f in frames:

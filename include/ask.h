@@ -89,6 +89,18 @@ typedef enum {
 #define ASK_FLAG_LEAF_TILED 16u   /* ASK: leaf kernel with one thread per pixel in
                                    * block_x x block_y tiles instead of the lane-refill
                                    * kernel (same map) */
+/* The paper's block-to-region mappings (Sec. 4.3), as comparison variants
+ * with the same map.  ASK_METHOD_ASK: one CTA of block_x * block_y threads
+ * per region for the perimeter query and the split; with ASK_FLAG_SBR
+ * (Sec. 4.3.1) that CTA also fills a uniform region and one CTA computes
+ * each leaf region; with ASK_FLAG_MBR (Sec. 4.3.2) fills and leaf pixels are
+ * spread over many blocks per region (fill list, tiled leaf kernel).
+ * ASK_METHOD_CDP2: ASK_FLAG_MBR makes uniform and leaf regions launch a
+ * multi-block child grid (DP-MBR); ASK_FLAG_SBR is the default DP mapping.
+ * The two flags exclude each other and ASK_FLAG_EXACT_BORDERS and
+ * ASK_FLAG_LEAF_TILED (ASK_EINVAL); the exhaustive method ignores them. */
+#define ASK_FLAG_SBR 32u
+#define ASK_FLAG_MBR 64u
 
 typedef struct {
     float re_min, re_max, im_min, im_max;

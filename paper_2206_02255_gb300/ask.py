@@ -24,6 +24,8 @@ FLAG_TIMING = 2
 FLAG_CDP2_FIRE_AND_FORGET = 4
 FLAG_EXACT_BORDERS = 8
 FLAG_LEAF_TILED = 16
+FLAG_SBR = 32
+FLAG_MBR = 64
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 

@@ -64,9 +64,11 @@ def sweep(ctx, window, n, max_dwell, space=None, reps=2, out=None):
     return res
 
 
-def model_choice(ctx, window, n, max_dwell, g, r, B, lam=10.0, q=None, c=128):
-    """The cost model's SBR-time optimum for this frame, with P estimated
-    from a counting render at (g, r, B) and q = the device's SM count."""
+def model_choice(ctx, window, n, max_dwell, g, r, B, lam=None, q=None, c=128, reps=3):
+    """The cost model's SBR-time optimum for this frame.  P is estimated from
+    a counting render at (g, r, B); lambda, unless given, is fitted (with the
+    model's time scale kappa) to the per-level and leaf device times of
+    `reps` timed renders there; q = the device's SM count."""
     import torch
     out = torch.empty((n, n), dtype=torch.int32, device="cuda:%d" % ctx.device)
     _, st = ctx.render("ask", window, n, max_dwell,
@@ -74,8 +76,21 @@ def model_choice(ctx, window, n, max_dwell, g, r, B, lam=10.0, q=None, c=128):
     P = costmodel.estimate_p(st)
     if q is None:
         q = torch.cuda.get_device_properties(ctx.device).multi_processor_count
+    kappa = None
+    if lam is None:
+        ctx.timing_read()  # forget older timed renders
+        p = ask.make_params(g, r, B, (16, 16), ask.FLAG_TIMING)
+        for _ in range(reps):
+            ctx.render("ask", window, n, max_dwell, p, out=out)
+        t = ctx.timing_read()
+        L = st["levels"]
+        R = max(1, t["renders"])
+        ms = [x / R for x in t["ms_per_level"][:L]] + [t["ms_leaf"] / R]
+        terms = costmodel.level_terms(n, g, r, max_dwell, q, c, st["regions_per_level"],
+                                      st["subdivisions_per_level"], st["leaves"], L)
+        kappa, lam = costmodel.fit_lambda(ms, terms)
     v, mg, mr, mB = costmodel.optimum(n, max_dwell, P, lam, q=q, c=c, scheme="sbr")
-    return dict(P=P, lam=lam, q=q, c=c, g=mg, r=mr, B=mB,
+    return dict(P=P, lam=lam, kappa_ms=kappa, q=q, c=c, g=mg, r=mr, B=mB,
                 model_speedup=costmodel.time_exhaustive(n, max_dwell, q, c) / v)
 
 

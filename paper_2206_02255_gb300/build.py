@@ -28,7 +28,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                       "-Xcompiler", "-ffp-contract=off", "--fmad=false", "-ftz=false",
                       "-prec-div=true", "-prec-sqrt=true", "-I", INCLUDE]
-PLAIN_UNITS = ["ask_api.cu", "ask_kernels.cu", "ask_noalloc.cu"]
+PLAIN_UNITS = ["ask_api.cu", "ask_kernels.cu", "ask_schemes.cu", "ask_noalloc.cu"]
 RDC_UNITS = ["ask_cdp2.cu"]
 
 

@@ -20,6 +20,10 @@ Time on q multiprocessors of c cores (Sec. 4.3):
 * SBR (one block of c cores per region), Delta[.] applied term by term
 * MBR (several blocks per region for the fills and the last level)
 
+lambda (the cost of one subdivision in units of A) is not given by the
+paper for a GPU; :func:`fit_lambda` fits it, with a time scale, to measured
+per-level times using :func:`level_terms`.
+
 tau is real-valued in the paper; here the sums run over the levels
 i = 0 .. floor(tau) - 2 and the powers of P use tau as given (a reading
 of the paper's notation, stated in the design notes).  Only plain
@@ -111,6 +115,52 @@ def optimum(n, A, P, lam, q=152, c=128, scheme="sbr", space=POW2):
         if best is None or v < best[0]:
             best = (v, g, r, B)
     return best
+
+
+def level_terms(n, g, r, A, q, c, regions, subdivs, leaves, levels):
+    """The SBR time of Sec. 4.3.1 level by level, with the measured region
+    and split counts in place of G R^i P^i and P: for level i with N_i
+    regions of nominal side s_i = n / (g r^i) and split fraction
+    P_i = splits_i / N_i,
+
+        T_i = (ceil(4 s_i / c) A + (1 - P_i) ceil(s_i^2 / c)) ceil(N_i / q)
+              + lambda * P_i A ceil(N_i / q),
+
+    returned as the pair (a_i, b_i) with T_i = a_i + lambda b_i; then the
+    last pass, A ceil(s_L^2 / c) ceil(N_leaf / q) with s_L the last level's
+    side, as (a_L, 0)."""
+    terms = []
+    for i in range(levels):
+        N = float(regions[i])
+        if N <= 0:
+            terms.append((0.0, 0.0))
+            continue
+        s_i = n / (g * float(r) ** i)
+        Pi = subdivs[i] / N
+        waves = _ceil(N / q)
+        a = (_ceil(4.0 * s_i / c) * A + (1.0 - Pi) * _ceil(s_i * s_i / c)) * waves
+        terms.append((a, Pi * A * waves))
+    s_L = n / (g * float(r) ** (levels - 1))
+    terms.append((A * _ceil(s_L * s_L / c) * _ceil(float(leaves) / q) if leaves else 0.0, 0.0))
+    return terms
+
+
+def fit_lambda(ms, terms):
+    """Least-squares fit of ms_i = kappa (a_i + lambda b_i) over the levels
+    and the last pass, kappa >= 0 and lambda >= 0.  ms: measured times in the
+    order of level_terms.  Returns (kappa in ms per model time unit,
+    lambda)."""
+    import numpy as np
+    X = np.array([[a, b] for a, b in terms], dtype=np.float64)
+    y = np.array(ms, dtype=np.float64)
+    sol, *_ = np.linalg.lstsq(X, y, rcond=None)
+    kappa, mu = float(sol[0]), float(sol[1])
+    if mu < 0.0 or kappa <= 0.0:
+        # refit with lambda = 0 (kappa alone)
+        mu = 0.0
+        den = float((X[:, 0] ** 2).sum())
+        kappa = float((X[:, 0] * y).sum() / den) if den > 0 else 0.0
+    return kappa, (mu / kappa if kappa > 0 else 0.0)
 
 
 def estimate_p(stats):

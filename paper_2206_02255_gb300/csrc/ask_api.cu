@@ -196,8 +196,13 @@ ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window,
     if (!block_ok(d.block_x, d.block_y))
         return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
     if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET |
-                    ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED))
+                    ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED | ASK_FLAG_SBR | ASK_FLAG_MBR))
         return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
+    if ((d.flags & ASK_FLAG_SBR) && (d.flags & ASK_FLAG_MBR))
+        return set_err(ctx, ASK_EINVAL, "ASK_FLAG_SBR and ASK_FLAG_MBR exclude each other");
+    if ((d.flags & (ASK_FLAG_SBR | ASK_FLAG_MBR)) && (d.flags & (ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED)))
+        return set_err(ctx, ASK_EINVAL,
+                       "ASK_FLAG_SBR / ASK_FLAG_MBR do not combine with EXACT_BORDERS or LEAF_TILED");
     if (method != ASK_METHOD_EXHAUSTIVE) {
         if (d.g == 0 || d.g > n)
             return set_err(ctx, ASK_EINVAL, "g must be in [1, n]");
@@ -257,16 +262,18 @@ ask_status grow(ask_ctx *ctx, T **buf, uint64_t *cap, uint64_t need, const char 
 }
 
 // Deferred fills can come from levels whose regions exceed the in-place size.
-uint64_t fill_need(const LevelPlan &plan)
+// Fill-list entries a render can append: the regions larger than the
+// in-place limit, or (MBR) every region of every level.
+uint64_t fill_need(const LevelPlan &plan, bool all = false)
 {
     uint64_t need = 0;
     for (uint32_t i = 0; i < plan.levels; ++i)
-        if ((uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
+        if (all || (uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
             need += plan.max_regions[i];
     return need;
 }
 
-ask_status reserve_ask(ask_ctx *ctx, const LevelPlan &plan)
+ask_status reserve_ask(ask_ctx *ctx, const LevelPlan &plan, bool fill_all = false)
 {
     uint64_t olt_need = 0, rst_need = 0;
     for (uint32_t i = 0; i < plan.levels; ++i) {
@@ -297,7 +304,8 @@ ask_status reserve_ask(ask_ctx *ctx, const LevelPlan &plan)
     }
     if ((st = grow(ctx, &ctx->leaves, &ctx->leaf_cap, leaf_need, "cudaMalloc(leaf list)")) != ASK_OK)
         return st;
-    if ((st = grow(ctx, &ctx->fills, &ctx->fill_cap, fill_need(plan), "cudaMalloc(fill list)")) != ASK_OK)
+    if ((st = grow(ctx, &ctx->fills, &ctx->fill_cap, fill_need(plan, fill_all), "cudaMalloc(fill list)")) !=
+        ASK_OK)
         return st;
     return ensure_counters(ctx);
 }
@@ -450,10 +458,16 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         // refused once device-runtime kernels have run, in which case the old
         // limit stays and a device launch that exceeds it is latched as an
         // error (never a hang or a fault).
-        uint64_t need = 1u << 18;
-        for (uint32_t i = 0; i < plan.levels; ++i)
+        // DP-MBR: every region may launch one child, so bound by the sum.
+        const bool mbr = (p.flags & ASK_FLAG_MBR) != 0;
+        uint64_t need = 1u << 18, sum = 0;
+        for (uint32_t i = 0; i < plan.levels; ++i) {
             if (plan.split[i] && plan.max_regions[i] > need)
                 need = plan.max_regions[i];
+            sum += plan.max_regions[i];
+        }
+        if (mbr && sum > need)
+            need = sum;
         if (need > (1u << 22))
             need = 1u << 22;
         if (need > ctx->cdp_pending) {
@@ -477,6 +491,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.B = p.B;
         a.count = count ? 1u : 0u;
         a.fire_and_forget = (p.flags & ASK_FLAG_CDP2_FIRE_AND_FORGET) ? 1u : 0u;
+        a.mbr = mbr ? 1u : 0u;
         a.ctr = ctx->ctr;
         if ((e = launch_cdp2(a, p.g, plan.side[0], p.block_x, p.block_y, s)) != cudaSuccess)
             return cuda_err(ctx, e, "CDP2 root kernel");
@@ -502,7 +517,12 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     }
 
     // ---- ASK: init, one level kernel per depth, fills, leaf kernel --------
-    if ((st = reserve_ask(ctx, plan)) != ASK_OK)
+    // The SBR / MBR mappings take whole regions per CTA: no chunked queries.
+    const bool sbr = (p.flags & ASK_FLAG_SBR) != 0, mbr = (p.flags & ASK_FLAG_MBR) != 0;
+    if (sbr || mbr)
+        for (uint32_t i = 0; i < plan.levels; ++i)
+            plan.chunks[i] = 1u;
+    if ((st = reserve_ask(ctx, plan, mbr)) != ASK_OK)
         return st;
     const int sms = ctx->dev.sms;
     const uint32_t L = plan.levels;
@@ -537,12 +557,16 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.fill_cap = (uint32_t)ctx->fill_cap;
         a.exact_last = exact ? 1u : 0u;
         a.ctr = ctx->ctr;
-        if ((e = launch_level(a, count, false, sms, s)) != cudaSuccess)
+        if (sbr || mbr)
+            e = launch_level_region(a, mbr, count, p.block_x * p.block_y, sms, s);
+        else
+            e = launch_level(a, count, false, sms, s);
+        if (e != cudaSuccess)
             return cuda_err(ctx, e, "level kernel");
         ++launches;
         mk.at(2 + (int)i, s);
     }
-    if (fill_need(plan) > 0) {
+    if (!sbr && fill_need(plan, mbr) > 0) {
         FillArgs f;
         f.map = d_dwell;
         f.n = n;
@@ -565,8 +589,12 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     la.leaf_cap = (uint32_t)ctx->leaf_cap;
     la.skip_perimeter = exact ? 1u : 0u;
     la.ctr = ctx->ctr;
-    if ((e = launch_leaf(la, p.block_x, p.block_y, count, (p.flags & ASK_FLAG_LEAF_TILED) != 0, false,
-                         sms, s)) != cudaSuccess)
+    if (sbr)
+        e = launch_leaf_region(la, p.block_x, p.block_y, count, sms, s);
+    else
+        e = launch_leaf(la, p.block_x, p.block_y, count, mbr || (p.flags & ASK_FLAG_LEAF_TILED) != 0, false,
+                        sms, s);
+    if (e != cudaSuccess)
         return cuda_err(ctx, e, "leaf kernel");
     ++launches;
     mk.at(3 + (int)L, s);

@@ -9,6 +9,10 @@
 // runs concurrently with its parent and siblings.  The host sees the render
 // complete when the whole tree of grids has completed.
 //
+// With ASK_FLAG_MBR (the DP-MBR scheme, Sec. 4.3.2) a region's fill and a
+// leaf region's pixels are not done by its own CTA either: it launches a
+// child grid of many blocks for them, into the same stream as its splits.
+//
 // This translation unit is compiled with relocatable device code and linked
 // against the device runtime; the rest of the library is not.
 #include <cuda_runtime.h>
@@ -30,6 +34,38 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     for (int o = 16; o > 0; o >>= 1)
         v += __shfl_xor_sync(kFull, v, o);
     return v;
+}
+
+// DP-MBR fill: block b writes rows [b * rows, b * rows + rows) of g.
+__global__ void __launch_bounds__(1024) cdp2_fill_kernel(uint32_t *map, uint32_t n, Region g,
+                                                         uint32_t v, uint32_t rows)
+{
+    Region band = g;
+    band.y0 = g.y0 + blockIdx.x * rows;
+    if (band.y0 >= g.y0 + g.h)
+        return;
+    band.h = min(rows, g.y0 + g.h - band.y0);
+    fill_rect(map, n, band, v, threadIdx.x, blockDim.x);
+}
+
+// DP-MBR leaf: one thread per interior pixel of g (its perimeter is already
+// written), block (blockIdx.x, blockIdx.y) covers one blockDim tile.
+__global__ void __launch_bounds__(1024) cdp2_pixel_kernel(CdpArgs a, Region g)
+{
+    const uint32_t px = g.x0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t py = g.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    unsigned long long it = 0;
+    if (px < g.x0 + g.w && py < g.y0 + g.h && !on_perimeter(g, px, py)) {
+        const float2 c = pixel_c(a.pm, px, py);
+        const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+        a.map[(size_t)py * a.n + px] = d;
+        it = d;
+    }
+    if (a.count) {
+        it = warp_sum_u64(it);
+        if (((threadIdx.x + threadIdx.y * blockDim.x) & 31u) == 0u && it)
+            atomicAdd(&a.ctr->iterations, it);
+    }
 }
 
 // One CTA = one region: child (blockIdx.x, blockIdx.y) of side `side` inside
@@ -114,7 +150,21 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
     }
 
     if (dmin == dmax) {
-        fill_rect(a.map, a.n, g, dmin, tid, T);
+        if (a.mbr) {
+            if (tid == 0) {
+                // about four pixels per thread of a block
+                const uint32_t rows = max(1u, (4u * T) / g.w);
+                const uint32_t nb = ceil_div_u32(g.h, rows);
+                if (a.fire_and_forget)
+                    cdp2_fill_kernel<<<nb, T, 0, cudaStreamFireAndForget>>>(a.map, a.n, g, dmin, rows);
+                else
+                    cdp2_fill_kernel<<<nb, T, 0, cudaStreamTailLaunch>>>(a.map, a.n, g, dmin, rows);
+                if (cudaGetLastError() != cudaSuccess)
+                    atomicOr(&a.ctr->error, ERR_DEVICE_LAUNCH);
+            }
+        } else {
+            fill_rect(a.map, a.n, g, dmin, tid, T);
+        }
         if (tid == 0)
             atomicAdd(&a.ctr->fills[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
     } else {
@@ -143,19 +193,35 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
                 perimeter_pixel(g, k, px, py);
                 a.map[(size_t)py * a.n + px] = stage[k];
             }
-            for (uint32_t ty0 = 0; ty0 < g.h; ty0 += blockDim.y) {
-                for (uint32_t tx0 = 0; tx0 < g.w; tx0 += blockDim.x) {
-                    const uint32_t px = g.x0 + tx0 + threadIdx.x, py = g.y0 + ty0 + threadIdx.y;
-                    if (px < g.x0 + g.w && py < g.y0 + g.h && !on_perimeter(g, px, py)) {
-                        const float2 c = pixel_c(a.pm, px, py);
-                        const uint32_t d = dwell(c.x, c.y, a.max_dwell);
-                        a.map[(size_t)py * a.n + px] = d;
-                        it += d;
+            if (a.mbr) {
+                if (tid == 0) {
+                    if (g.w > 2u && g.h > 2u) {
+                        const dim3 grid(ceil_div_u32(g.w, blockDim.x), ceil_div_u32(g.h, blockDim.y));
+                        const dim3 block(blockDim.x, blockDim.y);
+                        if (a.fire_and_forget)
+                            cdp2_pixel_kernel<<<grid, block, 0, cudaStreamFireAndForget>>>(a, g);
+                        else
+                            cdp2_pixel_kernel<<<grid, block, 0, cudaStreamTailLaunch>>>(a, g);
+                        if (cudaGetLastError() != cudaSuccess)
+                            atomicOr(&a.ctr->error, ERR_DEVICE_LAUNCH);
+                    }
+                    atomicAdd(&a.ctr->leaf_count, 1u);
+                }
+            } else {
+                for (uint32_t ty0 = 0; ty0 < g.h; ty0 += blockDim.y) {
+                    for (uint32_t tx0 = 0; tx0 < g.w; tx0 += blockDim.x) {
+                        const uint32_t px = g.x0 + tx0 + threadIdx.x, py = g.y0 + ty0 + threadIdx.y;
+                        if (px < g.x0 + g.w && py < g.y0 + g.h && !on_perimeter(g, px, py)) {
+                            const float2 c = pixel_c(a.pm, px, py);
+                            const uint32_t d = dwell(c.x, c.y, a.max_dwell);
+                            a.map[(size_t)py * a.n + px] = d;
+                            it += d;
+                        }
                     }
                 }
+                if (tid == 0)
+                    atomicAdd(&a.ctr->leaf_count, 1u);
             }
-            if (tid == 0)
-                atomicAdd(&a.ctr->leaf_count, 1u);
         }
     }
     if (a.count) {

@@ -156,10 +156,20 @@ struct CdpArgs {
     uint32_t r, B;
     uint32_t count;       // ASK_FLAG_COUNT
     uint32_t fire_and_forget;  // children into cudaStreamFireAndForget, not the tail stream
+    uint32_t mbr;              // DP-MBR: fills and leaf pixels by child grids
     DevCounters *ctr;
 };
 cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, uint32_t by,
                         cudaStream_t s);
 cudaError_t cdp2_set_pending_limit(size_t launches);
+
+// The paper's SBR / MBR mappings of ASK (Sec. 4.3.1-4.3.2), ask_schemes.cu.
+// One CTA of `threads` threads per region for the query and the split;
+// mbr = 0 fills in place, mbr = 1 appends uniform regions to the fill list.
+cudaError_t launch_level_region(const LevelArgs &a, bool mbr, bool count, uint32_t threads, int sms,
+                                cudaStream_t s);
+// SBR last level: one CTA (bx x by threads) per leaf region.
+cudaError_t launch_leaf_region(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, int sms,
+                               cudaStream_t s);
 
 }  // namespace ask

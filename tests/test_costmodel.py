@@ -69,3 +69,29 @@ def test_optimum_search_space_and_monotone_in_dwell():
 def test_estimate_p_from_counts():
     st = {"regions_per_level": [256, 2720, 27792], "subdivisions_per_level": [170, 1737, 0]}
     assert cm.estimate_p(st) == pytest.approx((170 + 1737) / (256 + 2720))
+
+
+def test_level_terms_by_hand():
+    # n = 64, g = 2, r = 2: level sides 32, 16; q = 4, c = 32, A = 10
+    t = cm.level_terms(64, 2, 2, 10.0, 4, 32, regions=[4, 8], subdivs=[2, 0], leaves=3, levels=2)
+    # level 0: s = 32, P = 1/2, waves = 1: ceil(128/32) 10 + 0.5 ceil(1024/32) = 40 + 16; b = 0.5 * 10
+    assert t[0] == pytest.approx((56.0, 5.0))
+    # level 1: s = 16, P = 0, waves = 2: (ceil(64/32) 10 + ceil(256/32)) 2 = (20 + 8) 2
+    assert t[1] == pytest.approx((56.0, 0.0))
+    # last pass: s_L = 16: 10 ceil(256/32) ceil(3/4) = 80
+    assert t[2] == pytest.approx((80.0, 0.0))
+
+
+def test_fit_lambda_recovers_planted_values():
+    terms = [(56.0, 5.0), (120.0, 20.0), (300.0, 11.0), (80.0, 0.0)]
+    kappa, lam = 0.002, 7.5
+    ms = [kappa * (a + lam * b) for a, b in terms]
+    k, l = cm.fit_lambda(ms, terms)
+    assert k == pytest.approx(kappa) and l == pytest.approx(lam)
+
+
+def test_fit_lambda_clamps_negative_lambda():
+    terms = [(10.0, 5.0), (20.0, 5.0), (30.0, 0.0)]
+    ms = [1.0, 2.0, 3.5]  # no subdivision cost at all: lambda must not go negative
+    k, l = cm.fit_lambda(ms, terms)
+    assert l >= 0.0 and k > 0.0

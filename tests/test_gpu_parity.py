@@ -75,9 +75,11 @@ def test_exhaustive_iteration_count(ctx, orc, asklib):
 # --------------------------------------------------------------------------
 # ASK
 # --------------------------------------------------------------------------
-def _check_ms(ctx, orc, asklib, method, win, n, M, g, r, B, block=(16, 16), counts=True):
+def _check_ms(ctx, orc, asklib, method, win, n, M, g, r, B, block=(16, 16), counts=True, flags=0):
     want, ost = orc.render_ms(win, n, M, g, r, B)
-    got, st = gpu_map(ctx, method, win, n, M, params(asklib, g, r, B, block), stats=True)
+    p = params(asklib, g, r, B, block)
+    p.flags |= flags
+    got, st = gpu_map(ctx, method, win, n, M, p, stats=True)
     d = first_diff(got, want)
     assert d is None, (method, win, n, M, g, r, B, block, d)
     if counts:
@@ -241,6 +243,71 @@ def test_cdp2_ragged(ctx, orc, asklib, n, g, r, B):
 
 
 # --------------------------------------------------------------------------
+# the paper's SBR / MBR mappings (Sec. 4.3) for ASK and for CDP2
+# --------------------------------------------------------------------------
+SCHEMES = ["SBR", "MBR"]
+SCHEME_RAGGED = [(1, 1, 2, 1), (5, 2, 2, 1), (37, 3, 2, 4), (257, 5, 3, 2), (1000, 7, 2, 8),
+                 (2048, 32, 4, 16), (3001, 11, 8, 3)]
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("block", inputs.BLOCK_SHAPES)
+def test_ask_scheme_c0(ctx, orc, asklib, scheme, block):
+    C = inputs.C0
+    _check_ms(ctx, orc, asklib, "ask", C["window"], C["n"], C["max_dwell"], C["g"], C["r"],
+              C["B"], block, flags=getattr(asklib, "FLAG_" + scheme))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("n,g,r,B", SCHEME_RAGGED)
+def test_ask_scheme_ragged(ctx, orc, asklib, scheme, n, g, r, B):
+    _check_ms(ctx, orc, asklib, "ask", inputs.WINDOW_WIDE, n, 300, g, r, B, (32, 4),
+              flags=getattr(asklib, "FLAG_" + scheme))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_ask_scheme_counters(ctx, orc, asklib, scheme):
+    """Both mappings evaluate whole leaves in the last pass and fill the
+    same pixels as the reference."""
+    C = inputs.C0
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    ex = orc.render_exhaustive(win, n, M)
+    want, ost, log = orc.render_ms(win, n, M, C["g"], C["r"], C["B"], log=True)
+    p = params(asklib, C["g"], C["r"], C["B"], (16, 16), count=True)
+    p.flags |= getattr(asklib, "FLAG_" + scheme)
+    got, st = gpu_map(ctx, "ask", win, n, M, p, stats=True)
+    assert np.array_equal(got, want)
+    assert st["fill_pixels"] == ost["fill_pixels"]
+    assert st["border_pixels"] == ost["border_pixels"]
+    leaf_px = leaf_it = 0
+    for e in log:
+        if e["kind"] == 2:
+            x0, y0, w, h = (int(e[k]) for k in ("x0", "y0", "w", "h"))
+            blk = ex[y0:y0 + h, x0:x0 + w].astype(np.uint64)
+            leaf_px += blk.size
+            leaf_it += int(blk.sum())
+    assert st["leaf_pixels"] == leaf_px
+    assert st["leaf_iterations"] == leaf_it
+    assert st["iterations"] == sum(st["iterations_per_level"]) + st["leaf_iterations"]
+
+
+@pytest.mark.parametrize("ff", [False, True], ids=["tail", "fire_and_forget"])
+@pytest.mark.parametrize("g,r,B,block", [(16, 2, 32, (16, 16)), (32, 4, 16, (64, 8)),
+                                         (8, 2, 16, (8, 8))])
+def test_cdp2_mbr_c0(ctx, orc, asklib, ff, g, r, B, block):
+    C = inputs.C0
+    f = asklib.FLAG_MBR | (asklib.FLAG_CDP2_FIRE_AND_FORGET if ff else 0)
+    _check_ms(ctx, orc, asklib, "cdp2", C["window"], C["n"], C["max_dwell"], g, r, B, block,
+              flags=f)
+
+
+@pytest.mark.parametrize("n,g,r,B", SCHEME_RAGGED[:5])
+def test_cdp2_mbr_ragged(ctx, orc, asklib, n, g, r, B):
+    _check_ms(ctx, orc, asklib, "cdp2", inputs.WINDOW_WIDE, n, 200, g, r, B, (16, 16),
+              flags=asklib.FLAG_MBR)
+
+
+# --------------------------------------------------------------------------
 # argument errors
 # --------------------------------------------------------------------------
 def _raw_render(ctx, asklib, method, win, n, M, p, ptr):
@@ -283,9 +350,11 @@ def test_invalid_arguments(ctx, asklib):
         (A, W, 8, 100, params(asklib, g=2, B=2), ptr + 4),      # not 16-byte aligned
         (E, W, 8, 100, params(asklib), ptr + 8),
     ]
-    flags_bad = params(asklib)
-    flags_bad.flags = 0x80
-    bad.append((A, W, 64, 100, flags_bad, ptr))
+    for f in (0x80, asklib.FLAG_SBR | asklib.FLAG_MBR,
+              asklib.FLAG_SBR | asklib.FLAG_EXACT_BORDERS, asklib.FLAG_MBR | asklib.FLAG_LEAF_TILED):
+        flags_bad = params(asklib)
+        flags_bad.flags = f
+        bad.append((A, W, 64, 100, flags_bad, ptr))
     for method, win, n, M, p, q in bad:
         st = _raw_render(ctx, asklib, method, win, n, M, p, q)
         assert st == asklib.EINVAL, (method, win, n, M, st)
@@ -328,6 +397,22 @@ def test_c1_cdp2_equals_ask(ctx, orc, asklib):
     c = gpu_map(ctx, "cdp2", *p, params(asklib, 32, 4, 16))
     assert first_diff(c, a) is None
     _sampled_regions(ctx, orc, asklib, "cdp2", *p, 32, 4, 16, (16, 16), k=3, seed=5, full=c)
+
+
+@pytest.mark.slow
+def test_c1_schemes_equal_ask(ctx, orc, asklib):
+    """ASK-SBR, ASK-MBR and DP-MBR give the default mapping's map at
+    n = 16384 (which is checked against the reference on sampled regions)."""
+    C = inputs.C1
+    p = (C["window"], C["n"], C["max_dwell"])
+    a = gpu_map(ctx, "ask", *p, params(asklib, 32, 4, 16))
+    for method, f in (("ask", asklib.FLAG_SBR), ("ask", asklib.FLAG_MBR),
+                      ("cdp2", asklib.FLAG_MBR | asklib.FLAG_CDP2_FIRE_AND_FORGET)):
+        q = params(asklib, 32, 4, 16, (32, 8))
+        q.flags |= f
+        b = gpu_map(ctx, method, *p, q)
+        assert first_diff(b, a) is None, (method, f)
+    _sampled_regions(ctx, orc, asklib, "ask", *p, 32, 4, 16, (16, 16), k=3, seed=11, full=a)
 
 
 @pytest.mark.slow
