@@ -110,7 +110,7 @@ struct LevelArgs {
     DevCounters *ctr;
 };
 // Perimeter pixels per work item of a level kernel.
-constexpr uint32_t kChunkPx = 128;
+constexpr uint32_t kChunkPx = 64;
 // Uniform regions larger than this are filled by the fill kernel.
 constexpr uint32_t kInPlaceFillArea = 16384;
 cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cudaStream_t s);

@@ -257,19 +257,7 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH>
     b.nchild = 0;
 }
 
-// Region state of a chunked query, read by lane 0 and broadcast.
-__device__ __forceinline__ uint2 read_state(const uint4 *st, uint32_t lane)
-{
-    uint2 v = make_uint2(kNone, 0u);
-    if (lane == 0) {
-        const volatile uint32_t *p = reinterpret_cast<const volatile uint32_t *>(st);
-        v.x = p[0];
-        v.y = p[1];
-    }
-    v.x = __shfl_sync(kFull, v.x, 0);
-    v.y = __shfl_sync(kFull, v.y, 0);
-    return v;
-}
+constexpr uint32_t kPollLag = 8;  // rounds between issuing a state load and using it
 
 // One chunk [k0, k1) of a large region's perimeter, queried by one warp.  The
 // region's state st: x = common dwell found so far (kNone: none yet),
@@ -280,9 +268,14 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
                                             uint32_t k1, uint4 *st, uint32_t lane,
                                             unsigned long long &it)
 {
+    const volatile uint32_t *ps = reinterpret_cast<const volatile uint32_t *>(st);
     for (uint32_t base = k0; base < k1; base += 32u) {
-        if (read_state(st, lane).y)
-            return;
+        // the state load is issued first; the group's set-up hides its latency
+        uint32_t sx = 0, sy = 0;
+        if (lane == 0) {
+            sx = ps[0];
+            sy = ps[1];
+        }
         const uint32_t k = base + lane;
         const bool active = k < k1;
         const unsigned amask = __ballot_sync(kFull, active);
@@ -291,14 +284,16 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
             perimeter_pixel(g, k, px, py);
         Orbit o = orbit_start(pixel_c(a.pm, px, py));
         bool done = !active, differ = false, stop = false;
-        uint2 v = read_state(st, lane);
-        const volatile uint32_t *ps = reinterpret_cast<const volatile uint32_t *>(st);
+        uint2 v = make_uint2(__shfl_sync(kFull, sx, 0), __shfl_sync(kFull, sy, 0));
+        if (v.y)
+            return;
+        // A state load is issued every kPollLag rounds and consumed kPollLag
+        // rounds later, so its L2 latency hides behind the updates of those
+        // rounds; a stale value is harmless (the common dwell is set once,
+        // the flag only rises).
+        uint32_t nx = v.x, ny = v.y, lag = 0;
         for (;;) {
-            // the next state load is issued now and consumed after the block,
-            // so its L2 latency hides behind the updates; a stale value is
-            // harmless (the common dwell is set once, the flag only rises)
-            uint32_t nx = 0, ny = 0;
-            if (lane == 0) {
+            if (lag == 0 && lane == 0) {
                 nx = ps[0];
                 ny = ps[1];
             }
@@ -312,11 +307,14 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
                 differ = true;
                 break;
             }
-            v.x = __shfl_sync(kFull, nx, 0);
-            v.y = __shfl_sync(kFull, ny, 0);
-            if (v.y) {
-                stop = true;
-                break;
+            if (++lag == kPollLag) {
+                lag = 0;
+                v.x = __shfl_sync(kFull, nx, 0);
+                v.y = __shfl_sync(kFull, ny, 0);
+                if (v.y) {
+                    stop = true;
+                    break;
+                }
             }
         }
         if (active)
