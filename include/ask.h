@@ -101,6 +101,8 @@ typedef enum {
  * ASK_FLAG_LEAF_TILED (ASK_EINVAL); the exhaustive method ignores them. */
 #define ASK_FLAG_SBR 32u
 #define ASK_FLAG_MBR 64u
+/* ask_render_host: render the whole map, then copy it (no banded pipeline). */
+#define ASK_FLAG_STAGED_COPY 128u
 
 typedef struct {
     float re_min, re_max, im_min, im_max;
@@ -130,8 +132,9 @@ typedef struct {
     uint64_t leaf_iterations;                  /* ASK_FLAG_COUNT, ASK: z-updates of the leaf kernel */
     float ms_total;                            /* device time of the render */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: device time of level kernel i */
-    float ms_leaf;                             /* ASK: device time of the leaf kernel */
-    float ms_fill;                             /* ASK: device time of the deferred-fill kernel */
+    float ms_leaf;                             /* ASK: leaf kernel, from the end of the levels */
+    float ms_fill;                             /* ASK: deferred-fill kernel, from the end of the
+                                                * levels (it runs beside the leaf kernel) */
     uint32_t kernel_launches;                  /* kernels this render launched from the host */
 } ask_stats;
 
@@ -145,8 +148,8 @@ typedef struct {
     float ms_total;                            /* whole renders */
     float ms_init;                             /* ASK: init kernel */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: level kernel i */
-    float ms_leaf;                             /* ASK: leaf kernel */
-    float ms_fill;                             /* ASK: deferred-fill kernel */
+    float ms_leaf;                             /* ASK: leaf kernel (from the end of the levels) */
+    float ms_fill;                             /* ASK: deferred-fill kernel (beside the leaf) */
 } ask_timing;
 
 typedef struct ask_ctx ask_ctx;
@@ -177,8 +180,13 @@ ask_status ask_render(ask_ctx *ctx, ask_method method, const ask_window *window,
                       uint32_t *d_dwell, void *stream, ask_stats *stats);
 
 /* Same as ask_render but the map lands in host memory h_dwell (n*n uint32,
- * pageable or pinned): the context renders into its own device buffer and
- * copies the result back on `stream`, then synchronises. */
+ * pageable or pinned; pinned is faster), and the call synchronises `stream`
+ * before returning.  The context renders into its own device buffer.  For
+ * ASK without stats (and without ASK_FLAG_STAGED_COPY) a map of 384 MiB or
+ * more is rendered in bands of initial-region rows -- independent
+ * subtrees that cover contiguous map rows -- and each band is copied to the
+ * host on a second stream while the next band renders; otherwise the whole
+ * map is rendered and then copied on `stream`.  The map is the same. */
 ask_status ask_render_host(ask_ctx *ctx, ask_method method, const ask_window *window,
                            uint32_t n, uint32_t max_dwell, const ask_params *params,
                            uint32_t *h_dwell, void *stream, ask_stats *stats);

@@ -26,6 +26,7 @@ FLAG_EXACT_BORDERS = 8
 FLAG_LEAF_TILED = 16
 FLAG_SBR = 32
 FLAG_MBR = 64
+FLAG_STAGED_COPY = 128
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 

@@ -3,6 +3,7 @@
 // of each method.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,9 +45,17 @@ struct ask_ctx {
     uint64_t fill_cap = 0;
     ask::DevCounters *ctr = nullptr;
     ask::DevCounters *h_ctr = nullptr;  // pinned mirror for stats
-    // device map for ask_render_host
+    // device map for ask_render_host (when the host buffer is not pinned)
     uint32_t *dmap = nullptr;
     size_t dmap_elems = 0;
+    // side stream on which the deferred-fill kernel runs beside the leaf
+    // kernel, and the events that fork it from and join it to the caller's
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // banded ask_render_host: copy stream and one event per band
+    static constexpr uint32_t kMaxBands = 64;
+    cudaStream_t cpy = nullptr;
+    cudaEvent_t band_ev[kMaxBands] = {};
     // events of the synchronous stats path: 0 = start, 1 = after init,
     // 2 + i = after level i, levels + 2 = after the leaf kernel
     cudaEvent_t ev[ASK_MAX_LEVELS + 4];
@@ -75,6 +84,9 @@ struct ask_graph {
 namespace ask {
 
 static uint32_t ceil_div(uint32_t a, uint32_t b) { return a / b + (a % b != 0u); }
+
+// Target bytes of map per band of the banded ask_render_host pipeline.
+constexpr uint64_t kBandBytes = 256ull << 20;
 
 bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
 {
@@ -196,7 +208,8 @@ ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window,
     if (!block_ok(d.block_x, d.block_y))
         return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
     if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET |
-                    ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED | ASK_FLAG_SBR | ASK_FLAG_MBR))
+                    ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED | ASK_FLAG_SBR | ASK_FLAG_MBR |
+                    ASK_FLAG_STAGED_COPY))
         return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
     if ((d.flags & ASK_FLAG_SBR) && (d.flags & ASK_FLAG_MBR))
         return set_err(ctx, ASK_EINVAL, "ASK_FLAG_SBR and ASK_FLAG_MBR exclude each other");
@@ -353,6 +366,39 @@ ask_status read_counters(ask_ctx *ctx, cudaStream_t s)
     return latched_error(ctx, err);
 }
 
+ask_status ensure_aux(ask_ctx *ctx)
+{
+    if (ctx->aux)
+        return ASK_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        ctx->aux = nullptr;
+        return cuda_err(ctx, e, "side stream");
+    }
+    return ASK_OK;
+}
+
+ask_status ensure_bands(ask_ctx *ctx)
+{
+    if (ctx->cpy)
+        return ASK_OK;
+    for (uint32_t b = 0; b < ask_ctx::kMaxBands; ++b) {
+        cudaError_t e = cudaEventCreateWithFlags(&ctx->band_ev[b], cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaEventCreate");
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->cpy, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        ctx->cpy = nullptr;
+        return cuda_err(ctx, e, "copy stream");
+    }
+    return ASK_OK;
+}
+
 ask_status ensure_ring(ask_ctx *ctx)
 {
     if (ctx->ring)
@@ -388,9 +434,11 @@ struct Marks {
     }
 };
 
+// ASK renders only the initial-region rows [row0, row0 + rows) when rows is
+// given (the banded host pipeline); every other method renders the frame.
 ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window, uint32_t n,
                        uint32_t max_dwell, const ask_params &p, uint32_t *d_dwell, cudaStream_t s,
-                       ask_stats *stats)
+                       ask_stats *stats, uint32_t row0 = 0, uint32_t rows = 0xffffffffu)
 {
     const bool count = (p.flags & ASK_FLAG_COUNT) != 0;
     const bool timing = (p.flags & ASK_FLAG_TIMING) != 0;
@@ -425,7 +473,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     if (method == ASK_METHOD_EXHAUSTIVE) {
         mk.at(0, s);
         if (count) {
-            if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
+            if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, 0, 0, s)) != cudaSuccess)
                 return cuda_err(ctx, e, "init kernel");
             ++launches;
         }
@@ -480,7 +528,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
             cudaGetLastError();  // a refused raise is not sticky
         }
         mk.at(0, s);
-        if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, s)) != cudaSuccess)
+        if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, 0, 0, s)) != cudaSuccess)
             return cuda_err(ctx, e, "init kernel");
         CdpArgs a;
         a.map = d_dwell;
@@ -528,8 +576,11 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     const uint32_t L = plan.levels;
     const bool exact = (p.flags & ASK_FLAG_EXACT_BORDERS) != 0;
     mk.at(0, s);
+    if (row0 >= plan.axis0)
+        return set_err(ctx, ASK_EINVAL, "band starts past the last initial-region row");
     if ((e = launch_init(ctx->olt[0], plan.chunks[0] > 1u ? ctx->rst[0] : nullptr, ctx->ctr, n,
-                         plan.side[0], plan.axis0, s)) != cudaSuccess)
+                         plan.side[0], plan.axis0, row0, std::min(rows, plan.axis0 - row0), s)) !=
+        cudaSuccess)
         return cuda_err(ctx, e, "init kernel");
     ++launches;
     mk.at(1, s);
@@ -566,7 +617,22 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         ++launches;
         mk.at(2 + (int)i, s);
     }
-    if (!sbr && fill_need(plan, mbr) > 0) {
+    // Marks: L + 1 = levels done (fill and leaf start), L + 2 = fill done,
+    // L + 3 = leaf done, L + 4 = render done.  With the default mapping the
+    // deferred fills (HBM writes) run on the side stream beside the leaf
+    // kernel (FP32 work): they write disjoint pixels and share no counters.
+    const bool fills = !sbr && fill_need(plan, mbr) > 0;
+    const bool side = fills && !mbr;
+    cudaStream_t fs = s;
+    if (side) {
+        if ((st = ensure_aux(ctx)) != ASK_OK)
+            return st;
+        fs = ctx->aux;
+        if ((e = cudaEventRecord(ctx->fork_ev, s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(fs, ctx->fork_ev, 0)) != cudaSuccess)
+            return cuda_err(ctx, e, "forking the fill stream");
+    }
+    if (fills) {
         FillArgs f;
         f.map = d_dwell;
         f.n = n;
@@ -574,11 +640,13 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         f.fill_cap = (uint32_t)ctx->fill_cap;
         f.max_rows = plan.side[0];
         f.ctr = ctx->ctr;
-        if ((e = launch_fill(f, false, sms, s)) != cudaSuccess)
+        // launched before the leaf kernel so its short-lived CTAs are resident
+        // first; the leaf kernel's CTAs take the slots they free
+        if ((e = launch_fill(f, false, sms, 0, fs)) != cudaSuccess)
             return cuda_err(ctx, e, "fill kernel");
         ++launches;
     }
-    mk.at(2 + (int)L, s);
+    mk.at(2 + (int)L, fs);
     LeafArgs la;
     la.map = d_dwell;
     la.n = n;
@@ -598,6 +666,12 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         return cuda_err(ctx, e, "leaf kernel");
     ++launches;
     mk.at(3 + (int)L, s);
+    if (side) {
+        if ((e = cudaEventRecord(ctx->join_ev, fs)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, ctx->join_ev, 0)) != cudaSuccess)
+            return cuda_err(ctx, e, "joining the fill stream");
+    }
+    mk.at(4 + (int)L, s);
     if (timing) {
         slot->levels = L;
         ++ctx->ring_head;
@@ -605,11 +679,11 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     if (stats) {
         if ((st = read_counters(ctx, s)) != ASK_OK)
             return st;
-        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[L + 3]);
+        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[L + 4]);
         for (uint32_t i = 0; i < L; ++i)
             cudaEventElapsedTime(&stats->ms_per_level[i], ctx->ev[i + 1], ctx->ev[i + 2]);
         cudaEventElapsedTime(&stats->ms_fill, ctx->ev[L + 1], ctx->ev[L + 2]);
-        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 2], ctx->ev[L + 3]);
+        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 1], ctx->ev[L + 3]);
         const DevCounters &c = *ctx->h_ctr;
         stats->levels = L;
         for (uint32_t i = 0; i < L; ++i) {
@@ -810,7 +884,7 @@ ask_status enqueue_batch(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &b
         f.max_rows = bp.max_rows;
         f.frames = b.frames;
         f.ctr = b.ctr;
-        if ((e = launch_fill(f, true, sms, s)) != cudaSuccess)
+        if ((e = launch_fill(f, true, sms, 0, s)) != cudaSuccess)
             return cuda_err(ctx, e, "batch fill kernel");
         ++n_launch;
     }
@@ -933,6 +1007,17 @@ void ask_ctx_destroy(ask_ctx *ctx)
         cudaFreeHost(ctx->h_ctr);
     if (ctx->dmap)
         cudaFree(ctx->dmap);
+    if (ctx->aux)
+        cudaStreamDestroy(ctx->aux);
+    if (ctx->cpy)
+        cudaStreamDestroy(ctx->cpy);
+    for (uint32_t b = 0; b < ask_ctx::kMaxBands; ++b)
+        if (ctx->band_ev[b])
+            cudaEventDestroy(ctx->band_ev[b]);
+    if (ctx->fork_ev)
+        cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev)
+        cudaEventDestroy(ctx->join_ev);
     if (ctx->events)
         for (int i = 0; i < ASK_MAX_LEVELS + 4; ++i)
             cudaEventDestroy(ctx->ev[i]);
@@ -1023,6 +1108,58 @@ ask_status ask_render_host(ask_ctx *ctx, ask_method method, const ask_window *wi
             return cuda_err(ctx, e, "cudaMalloc(device map)");
         ctx->dmap_elems = elems;
     }
+    // ASK without stats: the frame is rendered in bands of initial-region
+    // rows (independent subtrees, contiguous map rows); each band's rows go
+    // to the host on a copy stream while the next band renders.
+    LevelPlan plan;
+    uint32_t bands = 1;
+    if (method == ASK_METHOD_ASK && !stats && !(eff.flags & ASK_FLAG_STAGED_COPY) &&
+        make_plan(n, eff.g, eff.r, eff.B, &plan)) {
+        const uint64_t want = (elems * sizeof(uint32_t) + kBandBytes / 2) / kBandBytes;
+        bands = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(want, plan.axis0), ask_ctx::kMaxBands);
+        if (bands < 1)
+            bands = 1;
+    }
+    if (bands > 1) {
+        if ((st = ensure_bands(ctx)) != ASK_OK)
+            return st;
+        const uint32_t per = (plan.axis0 + bands - 1) / bands;  // initial-region rows per band
+        bands = (plan.axis0 + per - 1) / per;
+        auto copy_band = [&](uint32_t b) -> ask_status {
+            const size_t y0 = (size_t)b * per * plan.side[0];
+            const size_t y1 = std::min<size_t>(n, (size_t)(b + 1) * per * plan.side[0]);
+            cudaError_t e = cudaStreamWaitEvent(ctx->cpy, ctx->band_ev[b], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_dwell + y0 * n, ctx->dmap + y0 * n, (y1 - y0) * n * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, ctx->cpy);
+            return e == cudaSuccess ? ASK_OK : cuda_err(ctx, e, "copying a band of the map to the host");
+        };
+        // A copy into pinned memory is asynchronous, so band b - 1's copy is
+        // queued right after band b's render; a copy into pageable memory
+        // blocks the host, so every render is queued before the first copy.
+        cudaPointerAttributes pa;
+        const bool pinned = cudaPointerGetAttributes(&pa, h_dwell) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        for (uint32_t b = 0; b < bands; ++b) {
+            st = render_impl(ctx, method, window, n, max_dwell, eff, ctx->dmap, s, nullptr, b * per, per);
+            if (st != ASK_OK)
+                return st;
+            cudaError_t e = cudaEventRecord(ctx->band_ev[b], s);
+            if (e != cudaSuccess)
+                return cuda_err(ctx, e, "cudaEventRecord");
+            if (pinned && b > 0 && (st = copy_band(b - 1)) != ASK_OK)
+                return st;
+        }
+        for (uint32_t b = pinned ? bands - 1 : 0; b < bands; ++b)
+            if ((st = copy_band(b)) != ASK_OK)
+                return st;
+        cudaError_t e = cudaStreamSynchronize(ctx->cpy);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "copying the map to the host");
+        return read_counters(ctx, s);  // report latched device errors
+    }
     st = render_impl(ctx, method, window, n, max_dwell, eff, ctx->dmap, s, stats);
     if (st != ASK_OK)
         return st;
@@ -1050,7 +1187,7 @@ ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
     for (uint64_t k = ctx->ring_tail; k < ctx->ring_head; ++k) {
         const ask_ctx::TimingSlot &sl = ctx->ring[k % ask_ctx::kRing];
         const uint32_t L = sl.levels;
-        const int last = (sl.method == ASK_METHOD_ASK) ? (int)L + 3 : 1;
+        const int last = (sl.method == ASK_METHOD_ASK) ? (int)L + 4 : 1;
         float ms = 0.0f;
         if ((e = cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[last])) != cudaSuccess)
             return cuda_err(ctx, e, "cudaEventElapsedTime");
@@ -1064,7 +1201,7 @@ ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
             }
             cudaEventElapsedTime(&ms, sl.ev[L + 1], sl.ev[L + 2]);
             out->ms_fill += ms;
-            cudaEventElapsedTime(&ms, sl.ev[L + 2], sl.ev[L + 3]);
+            cudaEventElapsedTime(&ms, sl.ev[L + 1], sl.ev[L + 3]);
             out->ms_leaf += ms;
         }
         out->levels = L;

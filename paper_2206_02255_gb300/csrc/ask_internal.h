@@ -67,8 +67,11 @@ struct DeviceInfo {
 cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t max_dwell,
                               uint32_t bx, uint32_t by, bool count, DevCounters *ctr,
                               cudaStream_t s);
+// Zero the counters (except the latched error word) and, if olt0 is set,
+// write the initial regions of initial-region rows [row0, row0 + rows) of the
+// axis0 x axis0 grid of side s0 (count[0] = axis0 * rows).
 cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
-                        uint32_t axis0, cudaStream_t s);
+                        uint32_t axis0, uint32_t row0, uint32_t rows, cudaStream_t s);
 
 // One frame of a batch, resident on the device.  Region records of a batch
 // are uint4 {x0 | y0 << 16, (w-1) | (h-1) << 16, frame, 0}.
@@ -124,7 +127,8 @@ struct FillArgs {
     const FrameDesc *frames;
     DevCounters *ctr;
 };
-cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, cudaStream_t s);
+// grid <= 0: one resident wave over all SMs; else that many CTAs.
+cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, int grid, cudaStream_t s);
 cudaError_t launch_init_batch(uint4 *olt0, uint4 *rst0, DevCounters *ctr, const FrameDesc *frames,
                               uint32_t nframes, uint32_t total0, cudaStream_t s);
 

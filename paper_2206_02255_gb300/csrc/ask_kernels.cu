@@ -84,11 +84,11 @@ __global__ void __launch_bounds__(1024) exhaustive_kernel(uint32_t *__restrict__
 // level-0 OLT (the axis0 x axis0 non-empty initial regions of side s0) and,
 // when level 0 is queried in chunks, its per-region state.
 __global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, DevCounters *ctr,
-                            uint32_t n, uint32_t s0, uint32_t axis0)
+                            uint32_t n, uint32_t s0, uint32_t axis0, uint32_t row0, uint32_t rows)
 {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t total = axis0 * axis0;
+    const uint32_t total = axis0 * rows;
     if (ctr != nullptr) {
         uint32_t *w = reinterpret_cast<uint32_t *>(ctr);
         const uint32_t words = (uint32_t)(sizeof(DevCounters) / sizeof(uint32_t));
@@ -100,7 +100,7 @@ __global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, 
     if (olt0 == nullptr)
         return;
     for (uint32_t k = tid; k < total; k += stride) {
-        const uint32_t gx = k % axis0, gy = k / axis0;
+        const uint32_t gx = k % axis0, gy = row0 + k / axis0;
         const uint32_t x0 = gx * s0, y0 = gy * s0;
         olt0[k] = pack_region(x0, y0, min(s0, n - x0), min(s0, n - y0));
         if (rst0 != nullptr)
@@ -945,15 +945,15 @@ cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t m
 }
 
 cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
-                        uint32_t axis0, cudaStream_t s)
+                        uint32_t axis0, uint32_t row0, uint32_t rows, cudaStream_t s)
 {
-    const uint32_t total = axis0 * axis0;
+    const uint32_t total = axis0 * rows;
     uint32_t blocks = (total + 255u) / 256u;
     if (blocks < 1)
         blocks = 1;
     if (blocks > 4096)
         blocks = 4096;
-    init_kernel<<<blocks, 256, 0, s>>>(olt0, rst0, ctr, n, s0, axis0);
+    init_kernel<<<blocks, 256, 0, s>>>(olt0, rst0, ctr, n, s0, axis0, row0, rows);
     return cudaGetLastError();
 }
 
@@ -981,13 +981,15 @@ cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, cudaStream_t s)
+cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, int grid, cudaStream_t s)
 {
     if (batch) {
-        const int grid = persistent_grid(fill_kernel<true>, 256, 0, sms);
+        if (grid <= 0)
+            grid = persistent_grid(fill_kernel<true>, 256, 0, sms);
         fill_kernel<true><<<grid, 256, 0, s>>>(f);
     } else {
-        const int grid = persistent_grid(fill_kernel<false>, 256, 0, sms);
+        if (grid <= 0)
+            grid = persistent_grid(fill_kernel<false>, 256, 0, sms);
         fill_kernel<false><<<grid, 256, 0, s>>>(f);
     }
     return cudaGetLastError();

@@ -200,7 +200,7 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
     // error word here; the init kernel zeroes the rest and writes OLT 0
     if (cudaMemsetAsync(&sc->ctr->error, 0, sizeof(uint32_t), s) != cudaSuccess)
         return ASK_ECUDA;
-    if (launch_init(sc->olt[0], nullptr, sc->ctr, n, plan.side[0], plan.axis0, s) != cudaSuccess)
+    if (launch_init(sc->olt[0], nullptr, sc->ctr, n, plan.side[0], plan.axis0, 0u, plan.axis0, s) != cudaSuccess)
         return ASK_ECUDA;
     const uint32_t L = plan.levels;
     for (uint32_t i = 0; i < L; ++i) {

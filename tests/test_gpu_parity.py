@@ -226,6 +226,54 @@ def test_render_host(ctx, orc, asklib):
     assert np.array_equal(got, orc.render_exhaustive(win, n, M))
 
 
+@pytest.mark.parametrize("method", ["ask", "cdp2", "exhaustive"])
+def test_render_host_buffers(ctx, orc, asklib, method):
+    """Pinned, pageable and misaligned pinned host buffers, with and without
+    ASK_FLAG_STAGED_COPY, all get the reference map, also on a ragged n
+    whose rows are not a multiple of 16 bytes."""
+    import torch
+    for win, n, M, g, r, B in [(inputs.WINDOW_PAPER, 1024, 512, 16, 2, 32),
+                               (inputs.WINDOW_WIDE, 1001, 300, 7, 2, 8)]:
+        if method == "exhaustive":
+            want = orc.render_exhaustive(win, n, M)
+        else:
+            want, _ = orc.render_ms(win, n, M, g, r, B)
+        p = params(asklib, g, r, B)
+        pinned = torch.zeros((n, n), dtype=torch.int32, pin_memory=True)
+        got = ctx.render_host(method, win, n, M, p, out=pinned)
+        assert first_diff(got.numpy().view(np.uint32), want) is None, (method, n, "pinned")
+        big = torch.zeros(n * n + 4, dtype=torch.int32, pin_memory=True)
+        off = big[1:1 + n * n]  # 4 bytes past a 16-byte boundary
+        got = ctx.render_host(method, win, n, M, p, out=off)
+        assert first_diff(got.numpy().view(np.uint32).reshape(n, n), want) is None, (method, n, "unaligned")
+        pageable = np.zeros((n, n), dtype=np.uint32)
+        got = ctx.render_host(method, win, n, M, p, out=pageable)
+        assert first_diff(got, want) is None, (method, n, "pageable")
+        q = params(asklib, g, r, B)
+        q.flags |= asklib.FLAG_STAGED_COPY
+        pinned.zero_()
+        got = ctx.render_host(method, win, n, M, q, out=pinned)
+        assert first_diff(got.numpy().view(np.uint32), want) is None, (method, n, "staged")
+
+
+@pytest.mark.parametrize("n,g,r,B", [(12000, 8, 2, 32), (10500, 7, 3, 8), (16384, 64, 2, 16)])
+def test_render_host_banded(ctx, orc, asklib, n, g, r, B):
+    """Maps large enough for the banded host pipeline (several bands of
+    initial-region rows, a ragged last band) equal the device-output render,
+    into pinned and pageable buffers; sampled initial regions also equal the
+    reference."""
+    import torch
+    win, M = inputs.WINDOW_WIDE, 1000
+    p = params(asklib, g, r, B)
+    want = gpu_map(ctx, "ask", win, n, M, p)
+    pinned = torch.zeros((n, n), dtype=torch.int32, pin_memory=True)
+    got = ctx.render_host("ask", win, n, M, p, out=pinned).numpy().view(np.uint32)
+    assert first_diff(got, want) is None
+    pageable = np.zeros((n, n), dtype=np.uint32)
+    assert first_diff(ctx.render_host("ask", win, n, M, p, out=pageable), want) is None
+    _sampled_regions(ctx, orc, asklib, "ask", win, n, M, g, r, B, (16, 16), k=3, seed=n, full=got)
+
+
 # --------------------------------------------------------------------------
 # CDP2
 # --------------------------------------------------------------------------
