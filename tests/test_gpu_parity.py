@@ -398,7 +398,7 @@ def test_invalid_arguments(ctx, asklib):
         (A, W, 8, 100, params(asklib, g=2, B=2), ptr + 4),      # not 16-byte aligned
         (E, W, 8, 100, params(asklib), ptr + 8),
     ]
-    for f in (0x80, asklib.FLAG_SBR | asklib.FLAG_MBR,
+    for f in (0x100, asklib.FLAG_SBR | asklib.FLAG_MBR,
               asklib.FLAG_SBR | asklib.FLAG_EXACT_BORDERS, asklib.FLAG_MBR | asklib.FLAG_LEAF_TILED):
         flags_bad = params(asklib)
         flags_bad.flags = f
