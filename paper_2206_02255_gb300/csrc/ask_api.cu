@@ -88,7 +88,7 @@ static uint32_t ceil_div(uint32_t a, uint32_t b) { return a / b + (a % b != 0u);
 // Target bytes of map per band of the banded ask_render_host pipeline.
 constexpr uint64_t kBandBytes = 256ull << 20;
 
-bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
+bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px)
 {
     if (n == 0 || g == 0 || r < 2 || B == 0 || !plan)
         return false;
@@ -114,7 +114,7 @@ bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan)
         if (plan->max_regions[i] >= 0xffffffffull)
             return false;
         const uint64_t per = (s <= 2u) ? (uint64_t)s * s : 4ull * s - 4ull;
-        plan->chunks[i] = (uint32_t)((per + kChunkPx - 1) / kChunkPx);
+        plan->chunks[i] = (uint32_t)((per + chunk_px - 1) / chunk_px);
         if (plan->max_regions[i] * plan->chunks[i] >= 0xffffffffull)
             return false;
         const uint32_t sc = ceil_div(s, r);
@@ -742,7 +742,7 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
         if (!fr.d_dwell || ((uintptr_t)fr.d_dwell & 15u))
             return set_err(ctx, ASK_EINVAL, "frame %u: d_dwell must be 16-byte aligned", f);
         LevelPlan plan;
-        if (!make_plan(fr.n, fr.g, fr.r, fr.B, &plan))
+        if (!make_plan(fr.n, fr.g, fr.r, fr.B, &plan, kChunkPxBatch))
             return set_err(ctx, ASK_EINVAL, "frame %u: no valid subdivision plan", f);
         FrameDesc &d = bp.desc[f];
         std::memset(&d, 0, sizeof(d));

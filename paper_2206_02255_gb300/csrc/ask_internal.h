@@ -54,7 +54,8 @@ struct LevelPlan {
 
 // Fills `plan`; returns false if the parameters are invalid or a level could
 // hold 2^32 regions or more.
-bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan);
+// chunk_px: perimeter pixels per work item of the level kernels (chunks[i]).
+bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px = 64);
 
 // Launch configuration chosen per device at context creation.
 struct DeviceInfo {
@@ -112,8 +113,11 @@ struct LevelArgs {
     const FrameDesc *frames;  // batch: the frame table
     DevCounters *ctr;
 };
-// Perimeter pixels per work item of a level kernel.
+// Perimeter pixels per work item of a level kernel: one frame's top levels
+// have few regions and need the parallelism of small chunks; a batch has
+// regions enough, and there a chunk's fixed cost weighs more.
 constexpr uint32_t kChunkPx = 64;
+constexpr uint32_t kChunkPxBatch = 128;
 // Uniform regions larger than this are filled by the fill kernel.
 constexpr uint32_t kInPlaceFillArea = 16384;
 cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cudaStream_t s);

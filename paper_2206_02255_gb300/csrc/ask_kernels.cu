@@ -17,8 +17,9 @@
 //    region count from device memory and hand out work with an atomic
 //    counter, so no depth needs a host round trip;
 //  * a work item is one region's perimeter, or one chunk of kChunkPx
-//    perimeter pixels of a large region (several warps per region: the MBR
-//    mapping of Sec. 4.3.2 applied to the query), one warp per item;
+//    (kChunkPxBatch in a batch) perimeter pixels of a large region (several
+//    warps per region: the MBR mapping of Sec. 4.3.2 applied to the query),
+//    one warp per item;
 //  * a query stops at the first two perimeter dwells known to differ; warps
 //    of one region share that verdict through a per-region state word, and
 //    the warp that finishes the region's last chunk takes the decision;
@@ -257,13 +258,17 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH>
     b.nchild = 0;
 }
 
-constexpr uint32_t kPollLag = 8;  // rounds between issuing a state load and using it
+// Rounds between issuing a state load and using it, for one frame.  A
+// batch keeps enough warps resident to hide the load, and there a late
+// stop costs more than the wait, so it uses the value one round later.
+constexpr uint32_t kPollLag = 8;
 
 // One chunk [k0, k1) of a large region's perimeter, queried by one warp.  The
 // region's state st: x = common dwell found so far (kNone: none yet),
 // y = 1 once two dwells are known to differ, z = chunks finished.  Chunks of
 // the same region run on other warps at the same time and stop as soon as
 // one of them has set y.
+template <bool BATCH>
 __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uint32_t k0,
                                             uint32_t k1, uint4 *st, uint32_t lane,
                                             unsigned long long &it)
@@ -287,10 +292,10 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
         uint2 v = make_uint2(__shfl_sync(kFull, sx, 0), __shfl_sync(kFull, sy, 0));
         if (v.y)
             return;
-        // A state load is issued every kPollLag rounds and consumed kPollLag
-        // rounds later, so its L2 latency hides behind the updates of those
-        // rounds; a stale value is harmless (the common dwell is set once,
-        // the flag only rises).
+        // A state load is issued every kPollLag rounds (every round in a
+        // batch) and consumed that many rounds later, so its L2 latency
+        // hides behind the updates of those rounds; a stale value is
+        // harmless (the common dwell is set once, the flag only rises).
         uint32_t nx = v.x, ny = v.y, lag = 0;
         for (;;) {
             if (lag == 0 && lane == 0) {
@@ -307,7 +312,7 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
                 differ = true;
                 break;
             }
-            if (++lag == kPollLag) {
+            if (++lag == (BATCH ? 1u : kPollLag)) {
                 lag = 0;
                 v.x = __shfl_sync(kFull, nx, 0);
                 v.y = __shfl_sync(kFull, ny, 0);
@@ -450,12 +455,13 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
         } else {
             const uint32_t c = t - region * chunks;
             uint4 *st = a.rst_in + region;
-            const uint32_t k0 = min(P, c * kChunkPx), k1 = min(P, k0 + kChunkPx);
+            constexpr uint32_t CP = BATCH ? kChunkPxBatch : kChunkPx;
+            const uint32_t k0 = min(P, c * CP), k1 = min(P, k0 + CP);
             if (COUNT && lane == 0)
                 bpx += k1 - k0;
             if (k0 < k1) {
                 if (query)
-                    chunk_query(f, g, k0, k1, st, lane, it);
+                    chunk_query<BATCH>(f, g, k0, k1, st, lane, it);
                 else
                     chunk_exact(f, g, k0, k1, st, lane, it);
             }
