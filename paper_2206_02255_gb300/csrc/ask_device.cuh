@@ -104,45 +104,65 @@ __device__ __forceinline__ Orbit orbit_start(float2 c)
     return o;
 }
 
-// Advance an orbit by up to kUnroll updates without passing `limit`.
-// Returns true when it is finished: it escaped (o.d is its dwell) or it made
-// `limit` updates (o.d = limit: the dwell is at least limit).  A round never
-// finishes an orbit at o.d equal to the round's last count unless the state
-// there was tested, so orbits that are still running after a round have a
-// dwell strictly above the dwell of any orbit that finished in it.
-__device__ __forceinline__ bool orbit_round(Orbit &o, uint32_t limit)
+// Outcome of one round of an orbit.
+enum : uint32_t {
+    ORBIT_RUN = 0,   // every state so far passed; more rounds to go
+    ORBIT_DONE = 1,  // finished with o.d exact: escaped, or made `limit` updates
+    ORBIT_PEND = 2,  // escaped within the round's unchecked block: the dwell is in
+                     // (o.d, o.d + kUnroll], o keeps the block's starting state
+};
+
+// Advance an orbit by up to kUnroll updates without passing `limit`.  An
+// orbit still running after a round has made more updates than any orbit
+// that finished (or became pending) in it: its dwell is strictly larger.
+// A pending orbit needs orbit_resolve only if its exact dwell is wanted.
+__device__ __forceinline__ uint32_t orbit_step(Orbit &o, uint32_t limit)
 {
     if (o.d >= limit)
-        return true;
+        return ORBIT_DONE;
     if (o.fast && limit - o.d >= (uint32_t)kUnroll) {
         float x = o.x, y = o.y;
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k)
             z_update(x, y, o.cr, o.ci);
-        if (z_bounded(x, y)) {
-            o.x = x;
-            o.y = y;
-            o.d += (uint32_t)kUnroll;
-            return o.d >= limit;
-        }
-        // some state of this block escaped: replay the block with tests
-        for (int k = 0; k < kUnroll; ++k) {
-            if (!z_bounded(o.x, o.y))
-                return true;
-            z_update(o.x, o.y, o.cr, o.ci);
-            ++o.d;
-        }
-        return false;  // the block's last state escapes; the next round sees it
+        if (!z_bounded(x, y))
+            return ORBIT_PEND;
+        o.x = x;
+        o.y = y;
+        o.d += (uint32_t)kUnroll;
+        return o.d >= limit ? ORBIT_DONE : ORBIT_RUN;
     }
     for (int k = 0; k < kUnroll; ++k) {
-        if (o.d >= limit)
-            return true;
-        if (!z_bounded(o.x, o.y))
-            return true;
+        if (o.d >= limit || !z_bounded(o.x, o.y))
+            return ORBIT_DONE;
         z_update(o.x, o.y, o.cr, o.ci);
         ++o.d;
     }
-    return o.d >= limit;
+    return o.d >= limit ? ORBIT_DONE : ORBIT_RUN;
+}
+
+// Exact dwell of a pending orbit: its starting state z_d passed the test
+// and z_{d + kUnroll} failed; halving the gap finds the first failing state
+// (kUnroll - 1 updates, log2(kUnroll) tests, no branches that differ by lane).
+__device__ __forceinline__ void orbit_resolve(Orbit &o)
+{
+    float x = o.x, y = o.y;
+    uint32_t d = o.d;
+#pragma unroll
+    for (uint32_t h = (uint32_t)kUnroll / 2u; h >= 1u; h >>= 1) {
+        float tx = x, ty = y;
+#pragma unroll
+        for (uint32_t k = 0; k < h; ++k)
+            z_update(tx, ty, o.cr, o.ci);
+        if (z_bounded(tx, ty)) {
+            x = tx;
+            y = ty;
+            d += h;
+        }
+    }
+    o.x = x;
+    o.y = y;
+    o.d = d + 1u;
 }
 
 // Region record of the offset lookup tables (Sec. 5.2): origin and clipped
@@ -262,13 +282,13 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
         if (active)
             perimeter_pixel(g, k, px, py);
         Orbit o = orbit_start(pixel_c(pm, px, py));
-        bool done = !active;
+        uint32_t stt = active ? ORBIT_RUN : ORBIT_DONE;
         const uint32_t limit = have ? min(max_dwell, w + 1u) : max_dwell;
         bool differ = false;
         for (;;) {
-            if (!done)
-                done = orbit_round(o, limit);
-            const unsigned dm = __ballot_sync(kLaneMask, done) & amask;
+            if (stt == ORBIT_RUN)
+                stt = orbit_step(o, limit);
+            const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
             if (dm) {
@@ -276,6 +296,8 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
                 break;
             }
         }
+        if (!differ && stt == ORBIT_PEND)
+            orbit_resolve(o);
         if (active)
             it += o.d;
         if (differ)
@@ -314,15 +336,15 @@ __device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32
         if (active)
             perimeter_pixel(g, k, px, py);
         Orbit o = orbit_start(pixel_c(pm, px, py));
-        bool done = !active;
+        uint32_t stt = active ? ORBIT_RUN : ORBIT_DONE;
         bool differ = false, stop = false;
         for (;;) {
             // one value per warp, so every lane uses the same limit
             const uint32_t wv = __shfl_sync(kLaneMask, *vw, 0);
             const uint32_t limit = (wv != 0xffffffffu) ? min(max_dwell, wv + 1u) : max_dwell;
-            if (!done)
-                done = orbit_round(o, limit);
-            const unsigned dm = __ballot_sync(kLaneMask, done) & amask;
+            if (stt == ORBIT_RUN)
+                stt = orbit_step(o, limit);
+            const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
             if (dm) {
@@ -334,6 +356,8 @@ __device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32
                 break;
             }
         }
+        if (!stop && !differ && stt == ORBIT_PEND)
+            orbit_resolve(o);
         if (active)
             it += o.d;
         if (stop)

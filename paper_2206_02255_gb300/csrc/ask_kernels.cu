@@ -288,7 +288,8 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
         if (active)
             perimeter_pixel(g, k, px, py);
         Orbit o = orbit_start(pixel_c(a.pm, px, py));
-        bool done = !active, differ = false, stop = false;
+        uint32_t stt = active ? ORBIT_RUN : ORBIT_DONE;
+        bool differ = false, stop = false;
         uint2 v = make_uint2(__shfl_sync(kFull, sx, 0), __shfl_sync(kFull, sy, 0));
         if (v.y)
             return;
@@ -303,9 +304,9 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
                 ny = ps[1];
             }
             const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
-            if (!done)
-                done = orbit_round(o, limit);
-            const unsigned dm = __ballot_sync(kFull, done) & amask;
+            if (stt == ORBIT_RUN)
+                stt = orbit_step(o, limit);
+            const unsigned dm = __ballot_sync(kFull, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
             if (dm) {
@@ -322,6 +323,8 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
                 }
             }
         }
+        if (!stop && !differ && stt == ORBIT_PEND)
+            orbit_resolve(o);
         if (active)
             it += o.d;
         if (stop)
