@@ -109,30 +109,38 @@ enum : uint32_t {
     ORBIT_RUN = 0,   // every state so far passed; more rounds to go
     ORBIT_DONE = 1,  // finished with o.d exact: escaped, or made `limit` updates
     ORBIT_PEND = 2,  // escaped within the round's unchecked block: the dwell is in
-                     // (o.d, o.d + kUnroll], o keeps the block's starting state
+                     // (o.d, o.d + K], o keeps the block's starting state
 };
 
-// Advance an orbit by up to kUnroll updates without passing `limit`.  An
-// orbit still running after a round has made more updates than any orbit
-// that finished (or became pending) in it: its dwell is strictly larger.
-// A pending orbit needs orbit_resolve only if its exact dwell is wanted.
+// Updates per unchecked block of a perimeter-query round: a large region's
+// chunks (many rounds, few warps) take long rounds; a small region's whole
+// perimeter takes shorter ones, since its group ends after few rounds.
+constexpr uint32_t kQueryRoundLarge = 64;
+constexpr uint32_t kQueryRound = 32;
+
+// Advance an orbit by up to K updates (a power of two) without passing
+// `limit`.  An orbit still running after a round has made more updates than
+// any orbit that finished (or became pending) in it: its dwell is strictly
+// larger.  A pending orbit needs orbit_resolve only if its exact dwell is
+// wanted.
+template <uint32_t K>
 __device__ __forceinline__ uint32_t orbit_step(Orbit &o, uint32_t limit)
 {
     if (o.d >= limit)
         return ORBIT_DONE;
-    if (o.fast && limit - o.d >= (uint32_t)kUnroll) {
+    if (o.fast && limit - o.d >= K) {
         float x = o.x, y = o.y;
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k)
+        for (uint32_t k = 0; k < K; ++k)
             z_update(x, y, o.cr, o.ci);
         if (!z_bounded(x, y))
             return ORBIT_PEND;
         o.x = x;
         o.y = y;
-        o.d += (uint32_t)kUnroll;
+        o.d += K;
         return o.d >= limit ? ORBIT_DONE : ORBIT_RUN;
     }
-    for (int k = 0; k < kUnroll; ++k) {
+    for (uint32_t k = 0; k < K; ++k) {
         if (o.d >= limit || !z_bounded(o.x, o.y))
             return ORBIT_DONE;
         z_update(o.x, o.y, o.cr, o.ci);
@@ -141,15 +149,17 @@ __device__ __forceinline__ uint32_t orbit_step(Orbit &o, uint32_t limit)
     return o.d >= limit ? ORBIT_DONE : ORBIT_RUN;
 }
 
-// Exact dwell of a pending orbit: its starting state z_d passed the test
-// and z_{d + kUnroll} failed; halving the gap finds the first failing state
-// (kUnroll - 1 updates, log2(kUnroll) tests, no branches that differ by lane).
+// Exact dwell of an orbit left pending by orbit_step<K>: its starting state
+// z_d passed the test and z_{d + K} failed; halving the gap finds the first
+// failing state (K - 1 updates, log2(K) tests, no branches that differ by
+// lane).
+template <uint32_t K>
 __device__ __forceinline__ void orbit_resolve(Orbit &o)
 {
     float x = o.x, y = o.y;
     uint32_t d = o.d;
 #pragma unroll
-    for (uint32_t h = (uint32_t)kUnroll / 2u; h >= 1u; h >>= 1) {
+    for (uint32_t h = K / 2u; h >= 1u; h >>= 1) {
         float tx = x, ty = y;
 #pragma unroll
         for (uint32_t k = 0; k < h; ++k)
@@ -287,7 +297,7 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
         bool differ = false;
         for (;;) {
             if (stt == ORBIT_RUN)
-                stt = orbit_step(o, limit);
+                stt = orbit_step<kQueryRound>(o, limit);
             const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -297,7 +307,7 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
             }
         }
         if (!differ && stt == ORBIT_PEND)
-            orbit_resolve(o);
+            orbit_resolve<kQueryRound>(o);
         if (active)
             it += o.d;
         if (differ)
@@ -343,7 +353,7 @@ __device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32
             const uint32_t wv = __shfl_sync(kLaneMask, *vw, 0);
             const uint32_t limit = (wv != 0xffffffffu) ? min(max_dwell, wv + 1u) : max_dwell;
             if (stt == ORBIT_RUN)
-                stt = orbit_step(o, limit);
+                stt = orbit_step<kQueryRound>(o, limit);
             const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -357,7 +367,7 @@ __device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32
             }
         }
         if (!stop && !differ && stt == ORBIT_PEND)
-            orbit_resolve(o);
+            orbit_resolve<kQueryRound>(o);
         if (active)
             it += o.d;
         if (stop)

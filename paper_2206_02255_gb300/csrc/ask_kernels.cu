@@ -305,7 +305,7 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
             }
             const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
             if (stt == ORBIT_RUN)
-                stt = orbit_step(o, limit);
+                stt = orbit_step<kQueryRoundLarge>(o, limit);
             const unsigned dm = __ballot_sync(kFull, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
             }
         }
         if (!stop && !differ && stt == ORBIT_PEND)
-            orbit_resolve(o);
+            orbit_resolve<kQueryRoundLarge>(o);
         if (active)
             it += o.d;
         if (stop)
