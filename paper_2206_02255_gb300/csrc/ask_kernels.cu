@@ -628,9 +628,11 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 //    block's worth of updates left, parks (saved state, count, pixel) in the
 //    warp's buffer in shared memory and takes a new pixel at once;
 //  * when 32 orbits are parked, the warp finishes them together, one per
-//    lane: a binary search over the parked block (unchecked half blocks and
-//    one test each, the same number of steps on every lane) finds the exact
-//    escape, and the dwells are written.
+//    lane: a binary search over the parked block finds the exact escape
+//    (the block's midpoint state is parked too, so the first halving costs
+//    one test; then unchecked quarter, eighth, ... blocks and one test
+//    each, the same number of steps on every lane), and the dwells are
+//    written.
 // ---------------------------------------------------------------------------
 constexpr int kRefillWarps = 8;    // warps per CTA
 constexpr uint32_t kParkCap = 128; // parked orbits per warp (< 32 + 2 * 32)
@@ -662,12 +664,13 @@ __device__ __forceinline__ LView leaf_view(const LeafArgs &a, uint32_t frame)
     return v;
 }
 
-// Exact dwell of a parked orbit: state (x, y) after d updates, that state
-// known to pass the test, and "escaped, or d >= max_dwell" known to hold
-// kLeafUnroll updates later.  Points where escape is not absorbing take the
-// tested loop instead.  u = (count, py << 16 | px, frame).
+// Exact dwell of a parked orbit: s.xy = state after d updates, known to
+// pass the test, s.zw = the state kLeafUnroll / 2 updates later (the block's
+// midpoint), and "escaped, or d >= max_dwell" known to hold kLeafUnroll
+// updates later.  Points where escape is not absorbing take the tested loop
+// instead.  u = (count, py << 16 | px, frame).
 template <bool COUNT, bool BATCH>
-__device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint4 u,
+__device__ __forceinline__ void finish_parked(const LeafArgs &a, float4 s, uint4 u,
                                               unsigned long long &it)
 {
     const LView v = leaf_view<BATCH>(a, u.z);
@@ -682,9 +685,19 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float2 s, uint4
         }
     } else if (d < v.max_dwell) {
         // invariant: count d passes (d < max_dwell) and the predicate holds
-        // at d + 2h; halve h until the first count where it holds is d + 1
+        // at d + 2h; halve h until the first count where it holds is d + 1.
+        // The first halving uses the block's saved midpoint state.
+        {
+            const uint32_t h = (uint32_t)kLeafUnroll / 2u;
+            const bool hit = (v.max_dwell - d <= h) || !z_bounded(s.z, s.w);
+            if (!hit) {
+                x = s.z;
+                y = s.w;
+                d += h;
+            }
+        }
 #pragma unroll
-        for (uint32_t h = (uint32_t)kLeafUnroll / 2u; h >= 1u; h >>= 1) {
+        for (uint32_t h = (uint32_t)kLeafUnroll / 4u; h >= 1u; h >>= 1) {
             float tx = x, ty = y;
 #pragma unroll
             for (uint32_t k = 0; k < h; ++k)
@@ -742,11 +755,11 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
 {
     using R = Rec<BATCH>;
     using T = typename R::T;
-    __shared__ float2 park_s[kRefillWarps][kParkCap];  // saved state
+    __shared__ float4 park_s[kRefillWarps][kParkCap];  // saved state at the block's start and midpoint
     __shared__ uint4 park_u[kRefillWarps][kParkCap];   // count, pixel, frame
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    float2 *qs = park_s[wib];
+    float4 *qs = park_s[wib];
     uint4 *qu = park_u[wib];
     uint32_t parked = 0;  // warp-uniform
 
@@ -831,7 +844,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
         //      idle or parks this round are not used)
         const float sx0 = s0.x, sy0 = s0.y, sx1 = s1.x, sy1 = s1.y;
 #pragma unroll
-        for (int k = 0; k < kLeafUnroll; ++k) {
+        for (int k = 0; k < kLeafUnroll / 2; ++k) {
+            z_update(s0.x, s0.y, s0.cr, s0.ci);
+            z_update(s1.x, s1.y, s1.cr, s1.ci);
+        }
+        const float mx0 = s0.x, my0 = s0.y, mx1 = s1.x, my1 = s1.y;  // midpoint states
+#pragma unroll
+        for (int k = 0; k < kLeafUnroll / 2; ++k) {
             z_update(s0.x, s0.y, s0.cr, s0.ci);
             z_update(s1.x, s1.y, s1.cr, s1.ci);
         }
@@ -856,13 +875,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             const uint32_t n0 = (uint32_t)__popc(p0);
             if (park0) {
                 const uint32_t slot = parked + (uint32_t)__popc(p0 & lt_mask);
-                qs[slot] = make_float2(sx0, sy0);
+                qs[slot] = make_float4(sx0, sy0, mx0, my0);
                 qu[slot] = make_uint4(s0.d, s0.pix, f0, 0u);
                 s0.busy = false;
             }
             if (park1) {
                 const uint32_t slot = parked + n0 + (uint32_t)__popc(p1 & lt_mask);
-                qs[slot] = make_float2(sx1, sy1);
+                qs[slot] = make_float4(sx1, sy1, mx1, my1);
                 qu[slot] = make_uint4(s1.d, s1.pix, f1, 0u);
                 s1.busy = false;
             }
@@ -870,7 +889,7 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             __syncwarp();
             while (parked >= 32u) {
                 parked -= 32u;
-                const float2 sv = qs[parked + lane];
+                const float4 sv = qs[parked + lane];
                 const uint4 uv = qu[parked + lane];
                 __syncwarp();
                 finish_parked<COUNT, BATCH>(a, sv, uv, it);
