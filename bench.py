@@ -77,9 +77,11 @@ def parse():
     ap.add_argument("--max-dwell", type=int, default=None)
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the exhaustive and CDP2 comparison arms")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
-                    help="single: one n=16384 map per step (default); batch: 256 frames of "
-                         "mixed size and zoom per step; serve: Poisson render requests")
+    ap.add_argument("--workload", default="single", choices=["single", "large", "batch", "serve"],
+                    help="single: one n=16384 map per step (default); large: one n=65536, "
+                         "dwell 4096 map (17.2 GB) per step, tuned ASK vs exhaustive; batch: "
+                         "256 frames of mixed size and zoom per step; serve: Poisson render "
+                         "requests")
     ap.add_argument("--frames", type=int, default=256, help="batch: frames per step")
     return ap.parse_args()
 
@@ -121,6 +123,19 @@ def sum_over_ranks(world, value, device):
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def percentile(sorted_vals, q):
+    """q-th percentile (nearest rank) of an ascending list."""
+    if not sorted_vals:
+        return None
+    k = max(0, min(len(sorted_vals) - 1, int(round(q / 100.0 * len(sorted_vals) + 0.5)) - 1))
+    return sorted_vals[k]
+
+
+def finite(x):
+    """x, or None for NaN (a comparison arm that was not run)."""
+    return None if x != x else x
 
 
 def whole_job_rate(world, units, seconds, device):
@@ -254,7 +269,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    C = dict(inputs.C1)
+    large = args.workload == "large"
+    C = dict(inputs.C2 if large else inputs.C1)
     if args.n or args.max_dwell:
         C["n"] = args.n or C["n"]
         C["max_dwell"] = args.max_dwell or C["max_dwell"]
@@ -316,28 +332,35 @@ def run_gpu(args):
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
         one("ask", g, r, B, blk, ask.FLAG_TIMING)
-    e1.record(stream)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
-    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = ev[0].elapsed_time(ev[-1]) / args.steps
     ms_step = max_over_ranks(world, ms_step, dev)
+    per_step = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
+    step_pct = {"p50_ms": percentile(per_step, 50), "p99_ms": percentile(per_step, 99),
+                "min_ms": per_step[0], "max_ms": per_step[-1]}
     timing = ctx.timing_read()
 
     # ---- comparison arms, each tuned on its own (untimed for the headline)
     ms_ex = ms_cdp = ms_cdp_fnf = float("nan")
     ex_block = cdp_cfg = None
     if not args.no_compare:
-        reps = max(3, args.steps // 4)
+        reps = max(3, args.steps // 4) if not large else 3
         for blkx in inputs.BLOCK_SHAPES:
             t = time_renders("exhaustive", g, r, B, blkx, 2)
             if ex_block is None or t < ex_block[1]:
                 ex_block = (blkx, t)
         ms_ex = time_renders("exhaustive", g, r, B, ex_block[0], reps)
+    if not args.no_compare and not large:
+        # CDP2 arms: the n = 16384 comparison (the large map compares ASK with
+        # the exhaustive kernel only)
+        reps = max(3, args.steps // 4)
         fnf = ask.FLAG_CDP2_FIRE_AND_FORGET
         for cg in (8, 16, 32, 64):
             for cr in (2, 4):
@@ -351,7 +374,7 @@ def run_gpu(args):
         ms_cdp = time_renders("cdp2", cg, cr, cB, cblk, 1)
     # ---- the paper's SBR / MBR mappings (Sec. 4.3), each tuned on its own
     schemes = None
-    if not args.no_compare:
+    if not args.no_compare and not large:
         reps = max(3, args.steps // 4)
         schemes = {"ask_default": {"ms": ms_step, "g": g, "r": r, "B": B, "block": list(blk)}}
         space = [(sg, sr, sB, sblk) for sg in (8, 16, 32, 64) for sr in (2, 4)
@@ -378,7 +401,7 @@ def run_gpu(args):
 
     # ---- cost model (Sec. 4) beside the tuner and the paper's configurations
     model = None
-    if not args.no_compare:
+    if not args.no_compare and not large:
         from paper_2206_02255_gb300 import autotune
         mc = autotune.model_choice(ctx, win, n, M, g, r, B)
         model = {"P": mc["P"], "lambda_fit": mc["lam"], "kappa_ms": mc["kappa_ms"],
@@ -421,6 +444,31 @@ def run_gpu(args):
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (
             sms * 128 * clk["sm_mhz"] * 1e6 / FP32_OPS_PER_ITER / 1e9)
+
+    # ---- the deferred-fill kernel against HBM write bandwidth --------------
+    # algorithmic bytes: 4 per pixel of the regions it fills (large uniform
+    # regions; small ones are filled inside the level kernels)
+    # the fill kernel is timed alone (ASK_FLAG_SERIAL_FILL: on the render
+    # stream, every SM), since beside the leaf kernel it shares the SMs
+    roofline_fill = None
+    for _ in range(5):
+        one("ask", g, r, B, blk, ask.FLAG_TIMING | ask.FLAG_SERIAL_FILL)
+    tser = ctx.timing_read()
+    ms_fill = tser["ms_fill"] / tser["renders"]
+    if cst.get("deferred_fill_pixels") and ms_fill > 0:
+        hbm = 6793.4
+        try:
+            hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        except Exception:
+            pass
+        fb = 4.0 * cst["deferred_fill_pixels"]
+        roofline_fill = {"bound": "hbm", "kernel": "fill", "achieved": fb / (ms_fill / 1e3) / 1e9,
+                         "peak": hbm, "unit": "GB/s", "frac": fb / (ms_fill / 1e3) / 1e9 / hbm,
+                         "bytes_per_launch": fb, "ms": ms_fill,
+                         "render_ms_with_serial_fill": tser["ms_total"] / tser["renders"],
+                         "traffic": recorded_traffic("fill_kernel", C["name"])
+                         if (g, r, B) == (16, 4, 16) else None,
+                         "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     # ---- end to end through the C ABI with a host buffer -------------------
     e2e = None
@@ -467,15 +515,16 @@ def run_gpu(args):
                        "l2": "output map %.2f GB > 129 MB L2, rewritten every step" % (pixels * 4 / 1e9)},
             "dwell_iter_s": {"executed": cst["iterations"] / (ms_step / 1e3),
                              "exhaustive_equivalent": est["iterations"] / (ms_step / 1e3)},
-            "exhaustive": {"ms": ms_ex, "gpix_s": pixels / (ms_ex / 1e3) / 1e9,
-                           "dwell_iter_s": est["iterations"] / (ms_ex / 1e3),
+            "step_ms": step_pct,
+            "exhaustive": {"ms": finite(ms_ex), "gpix_s": finite(pixels / (ms_ex / 1e3) / 1e9),
+                           "dwell_iter_s": finite(est["iterations"] / (ms_ex / 1e3)),
                            "block": list(ex_block[0]) if ex_block else None},
-            "cdp2": {"ms_tail_launch": ms_cdp, "ms_fire_and_forget": ms_cdp_fnf,
-                     "gpix_s": pixels / (min(ms_cdp, ms_cdp_fnf) / 1e3) / 1e9,
-                     "tuned": ({"g": cdp_cfg[0], "r": cdp_cfg[1], "B": cdp_cfg[2],
-                                "block": list(cdp_cfg[3])} if cdp_cfg else None)},
-            "speedup_vs_exhaustive": ms_ex / ms_step,
-            "speedup_vs_cdp2": min(ms_cdp, ms_cdp_fnf) / ms_step,
+            "cdp2": ({"ms_tail_launch": ms_cdp, "ms_fire_and_forget": ms_cdp_fnf,
+                      "gpix_s": pixels / (min(ms_cdp, ms_cdp_fnf) / 1e3) / 1e9,
+                      "tuned": {"g": cdp_cfg[0], "r": cdp_cfg[1], "B": cdp_cfg[2],
+                                "block": list(cdp_cfg[3])}} if cdp_cfg else None),
+            "speedup_vs_exhaustive": finite(ms_ex / ms_step),
+            "speedup_vs_cdp2": finite(min(ms_cdp, ms_cdp_fnf) / ms_step),
             "mismatch_vs_exhaustive_pixels": mismatch,
             "schemes": schemes, "cost_model": model,
             "kernels_ms": kern, "levels": cst["levels"],
@@ -483,7 +532,8 @@ def run_gpu(args):
             "fills_per_level": cst["fills_per_level"],
             "iterations_per_level": cst["iterations_per_level"],
             "leaf_iterations": cst["leaf_iterations"],
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_fill": roofline_fill,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "tune_sweep_top5": sorted(sweep, key=lambda t: t[3])[:5],

@@ -103,6 +103,11 @@ typedef enum {
 #define ASK_FLAG_MBR 64u
 /* ask_render_host: render the whole map, then copy it (no banded pipeline). */
 #define ASK_FLAG_STAGED_COPY 128u
+/* ASK: run the deferred-fill kernel alone, on the render stream before the
+ * leaf kernel, over every SM (by default it runs beside the leaf kernel on a
+ * second stream); the same map.  With ASK_FLAG_TIMING this times the fill
+ * kernel by itself. */
+#define ASK_FLAG_SERIAL_FILL 256u
 
 typedef struct {
     float re_min, re_max, im_min, im_max;
@@ -132,10 +137,16 @@ typedef struct {
     uint64_t leaf_iterations;                  /* ASK_FLAG_COUNT, ASK: z-updates of the leaf kernel */
     float ms_total;                            /* device time of the render */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: device time of level kernel i */
-    float ms_leaf;                             /* ASK: leaf kernel, from the end of the levels */
+    float ms_leaf;                             /* ASK: leaf kernel, from the end of the levels
+                                                * (from the end of the fill kernel when that
+                                                * runs first: ASK_FLAG_SERIAL_FILL, MBR) */
     float ms_fill;                             /* ASK: deferred-fill kernel, from the end of the
-                                                * levels (it runs beside the leaf kernel) */
+                                                * levels (by default it runs beside the leaf
+                                                * kernel) */
     uint32_t kernel_launches;                  /* kernels this render launched from the host */
+    uint32_t pad2_;
+    uint64_t deferred_fill_pixels;             /* ASK_FLAG_COUNT, ASK: pixels of the uniform
+                                                * regions left to the deferred-fill kernel */
 } ask_stats;
 
 /* Per-kernel device time summed over the renders made with ASK_FLAG_TIMING
@@ -148,8 +159,8 @@ typedef struct {
     float ms_total;                            /* whole renders */
     float ms_init;                             /* ASK: init kernel */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: level kernel i */
-    float ms_leaf;                             /* ASK: leaf kernel (from the end of the levels) */
-    float ms_fill;                             /* ASK: deferred-fill kernel (beside the leaf) */
+    float ms_leaf;                             /* ASK: leaf kernel (as in ask_stats) */
+    float ms_fill;                             /* ASK: deferred-fill kernel (as in ask_stats) */
 } ask_timing;
 
 typedef struct ask_ctx ask_ctx;

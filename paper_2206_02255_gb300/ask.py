@@ -27,6 +27,7 @@ FLAG_LEAF_TILED = 16
 FLAG_SBR = 32
 FLAG_MBR = 64
 FLAG_STAGED_COPY = 128
+FLAG_SERIAL_FILL = 256
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 
@@ -53,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("iterations_per_level", ctypes.c_uint64 * ASK_MAX_LEVELS),
                 ("leaf_iterations", ctypes.c_uint64), ("ms_total", ctypes.c_float),
                 ("ms_per_level", ctypes.c_float * ASK_MAX_LEVELS), ("ms_leaf", ctypes.c_float),
-                ("ms_fill", ctypes.c_float), ("kernel_launches", ctypes.c_uint32)]
+                ("ms_fill", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
+                ("pad2_", ctypes.c_uint32), ("deferred_fill_pixels", ctypes.c_uint64)]
 
     def as_dict(self):
         L = self.levels
@@ -69,6 +71,7 @@ class Stats(ctypes.Structure):
             "leaf_iterations": self.leaf_iterations, "ms_total": self.ms_total,
             "ms_per_level": list(self.ms_per_level[:L]), "ms_leaf": self.ms_leaf,
             "ms_fill": self.ms_fill, "kernel_launches": self.kernel_launches,
+            "deferred_fill_pixels": self.deferred_fill_pixels,
         }
 
 

@@ -48,10 +48,6 @@ struct ask_ctx {
     // device map for ask_render_host (when the host buffer is not pinned)
     uint32_t *dmap = nullptr;
     size_t dmap_elems = 0;
-    // side stream on which the deferred-fill kernel runs beside the leaf
-    // kernel, and the events that fork it from and join it to the caller's
-    cudaStream_t aux = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // banded ask_render_host: copy stream and one event per band
     static constexpr uint32_t kMaxBands = 64;
     cudaStream_t cpy = nullptr;
@@ -209,7 +205,7 @@ ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window,
         return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
     if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET |
                     ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED | ASK_FLAG_SBR | ASK_FLAG_MBR |
-                    ASK_FLAG_STAGED_COPY))
+                    ASK_FLAG_STAGED_COPY | ASK_FLAG_SERIAL_FILL))
         return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
     if ((d.flags & ASK_FLAG_SBR) && (d.flags & ASK_FLAG_MBR))
         return set_err(ctx, ASK_EINVAL, "ASK_FLAG_SBR and ASK_FLAG_MBR exclude each other");
@@ -275,14 +271,15 @@ ask_status grow(ask_ctx *ctx, T **buf, uint64_t *cap, uint64_t need, const char 
 }
 
 // Deferred fills can come from levels whose regions exceed the in-place size.
-// Fill-list entries a render can append: the regions larger than the
-// in-place limit, or (MBR) every region of every level.
+// Fill-list entries a render can append: the bands of the regions larger
+// than the in-place limit, or (MBR) of every region of every level.  A
+// clipped region has no more bands than a full one of its level.
 uint64_t fill_need(const LevelPlan &plan, bool all = false)
 {
     uint64_t need = 0;
     for (uint32_t i = 0; i < plan.levels; ++i)
         if (all || (uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
-            need += plan.max_regions[i];
+            need += plan.max_regions[i] * fill_band_count(plan.side[i], plan.side[i]);
     return need;
 }
 
@@ -364,22 +361,6 @@ ask_status read_counters(ask_ctx *ctx, cudaStream_t s)
             return cuda_err(ctx, e, "clearing the device error word");
     }
     return latched_error(ctx, err);
-}
-
-ask_status ensure_aux(ask_ctx *ctx)
-{
-    if (ctx->aux)
-        return ASK_OK;
-    cudaError_t e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        ctx->aux = nullptr;
-        return cuda_err(ctx, e, "side stream");
-    }
-    return ASK_OK;
 }
 
 ask_status ensure_bands(ask_ctx *ctx)
@@ -619,34 +600,25 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     }
     // Marks: L + 1 = levels done (fill and leaf start), L + 2 = fill done,
     // L + 3 = leaf done, L + 4 = render done.  With the default mapping the
-    // deferred fills (HBM writes) run on the side stream beside the leaf
-    // kernel (FP32 work): they write disjoint pixels and share no counters.
+    // deferred fills (HBM writes) ride along the lane-refill leaf kernel
+    // (FP32 work): its warps write one band of the fill list every few
+    // rounds.  The tiled leaf kernel, the MBR mapping and
+    // ASK_FLAG_SERIAL_FILL run the fill kernel alone first.
+    const bool tiled = mbr || (p.flags & ASK_FLAG_LEAF_TILED) != 0;
     const bool fills = !sbr && fill_need(plan, mbr) > 0;
-    const bool side = fills && !mbr;
-    cudaStream_t fs = s;
-    if (side) {
-        if ((st = ensure_aux(ctx)) != ASK_OK)
-            return st;
-        fs = ctx->aux;
-        if ((e = cudaEventRecord(ctx->fork_ev, s)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(fs, ctx->fork_ev, 0)) != cudaSuccess)
-            return cuda_err(ctx, e, "forking the fill stream");
-    }
-    if (fills) {
+    const bool fused = fills && !tiled && !(p.flags & ASK_FLAG_SERIAL_FILL);
+    if (fills && !fused) {
         FillArgs f;
         f.map = d_dwell;
         f.n = n;
         f.fills = ctx->fills;
         f.fill_cap = (uint32_t)ctx->fill_cap;
-        f.max_rows = plan.side[0];
         f.ctr = ctx->ctr;
-        // launched before the leaf kernel so its short-lived CTAs are resident
-        // first; the leaf kernel's CTAs take the slots they free
-        if ((e = launch_fill(f, false, sms, 0, fs)) != cudaSuccess)
+        if ((e = launch_fill(f, false, sms, s)) != cudaSuccess)
             return cuda_err(ctx, e, "fill kernel");
         ++launches;
     }
-    mk.at(2 + (int)L, fs);
+    mk.at(2 + (int)L, s);
     LeafArgs la;
     la.map = d_dwell;
     la.n = n;
@@ -656,21 +628,17 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     la.leaves = ctx->leaves;
     la.leaf_cap = (uint32_t)ctx->leaf_cap;
     la.skip_perimeter = exact ? 1u : 0u;
+    la.fills = fused ? ctx->fills : nullptr;
+    la.fill_cap = fused ? (uint32_t)ctx->fill_cap : 0u;
     la.ctr = ctx->ctr;
     if (sbr)
         e = launch_leaf_region(la, p.block_x, p.block_y, count, sms, s);
     else
-        e = launch_leaf(la, p.block_x, p.block_y, count, mbr || (p.flags & ASK_FLAG_LEAF_TILED) != 0, false,
-                        sms, s);
+        e = launch_leaf(la, p.block_x, p.block_y, count, tiled, false, sms, s);
     if (e != cudaSuccess)
         return cuda_err(ctx, e, "leaf kernel");
     ++launches;
     mk.at(3 + (int)L, s);
-    if (side) {
-        if ((e = cudaEventRecord(ctx->join_ev, fs)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s, ctx->join_ev, 0)) != cudaSuccess)
-            return cuda_err(ctx, e, "joining the fill stream");
-    }
     mk.at(4 + (int)L, s);
     if (timing) {
         slot->levels = L;
@@ -683,7 +651,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         for (uint32_t i = 0; i < L; ++i)
             cudaEventElapsedTime(&stats->ms_per_level[i], ctx->ev[i + 1], ctx->ev[i + 2]);
         cudaEventElapsedTime(&stats->ms_fill, ctx->ev[L + 1], ctx->ev[L + 2]);
-        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 1], ctx->ev[L + 3]);
+        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[L + 2], ctx->ev[L + 3]);
         const DevCounters &c = *ctx->h_ctr;
         stats->levels = L;
         for (uint32_t i = 0; i < L; ++i) {
@@ -694,6 +662,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         }
         stats->leaves = c.leaf_count;
         stats->fill_pixels = c.fill_pixels;
+        stats->deferred_fill_pixels = c.deferred_fill_pixels;
         stats->leaf_pixels = c.leaf_pixels;
         stats->border_pixels = c.border_pixels;
         stats->iterations = c.iterations;
@@ -711,7 +680,7 @@ struct BatchPlan {
     uint32_t L = 0;                       // deepest level over the frames
     uint32_t chunks[ASK_MAX_LEVELS] = {};  // chunks per region at each level (max over frames)
     uint64_t olt_need = 0, leaf_need = 0, rst_need = 0, fill_need = 0;
-    uint32_t total0 = 0, max_rows = 0;
+    uint32_t total0 = 0;
 };
 
 ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, uint32_t flags,
@@ -761,14 +730,12 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
             if (plan.chunks[i] > bp.chunks[i])
                 bp.chunks[i] = plan.chunks[i];
             if ((uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
-                bp.fill_need += plan.max_regions[i];
+                bp.fill_need += plan.max_regions[i] * fill_band_count(plan.side[i], plan.side[i]);
         }
         bp.leaf_need += plan.max_regions[plan.levels - 1];
         total0 += (uint64_t)plan.axis0 * plan.axis0;
         if (plan.levels > bp.L)
             bp.L = plan.levels;
-        if (plan.side[0] > bp.max_rows)
-            bp.max_rows = plan.side[0];
     }
     for (uint32_t i = 0; i < bp.L; ++i) {
         if (level_regions[i] * bp.chunks[i] >= 0xffffffffull)
@@ -876,20 +843,11 @@ ask_status enqueue_batch(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &b
             return cuda_err(ctx, e, "batch level kernel");
         ++n_launch;
     }
-    if (bp.fill_need) {
-        FillArgs f;
-        std::memset(&f, 0, sizeof(f));
-        f.fills = b.fills;
-        f.fill_cap = (uint32_t)b.fill_cap;
-        f.max_rows = bp.max_rows;
-        f.frames = b.frames;
-        f.ctr = b.ctr;
-        if ((e = launch_fill(f, true, sms, 0, s)) != cudaSuccess)
-            return cuda_err(ctx, e, "batch fill kernel");
-        ++n_launch;
-    }
+    // the deferred fills ride along the leaf kernel
     LeafArgs la;
     std::memset(&la, 0, sizeof(la));
+    la.fills = bp.fill_need ? b.fills : nullptr;
+    la.fill_cap = bp.fill_need ? (uint32_t)b.fill_cap : 0u;
     la.leaves = b.leaves;
     la.leaf_cap = (uint32_t)b.leaf_cap;
     la.skip_perimeter = exact ? 1u : 0u;
@@ -1007,17 +965,11 @@ void ask_ctx_destroy(ask_ctx *ctx)
         cudaFreeHost(ctx->h_ctr);
     if (ctx->dmap)
         cudaFree(ctx->dmap);
-    if (ctx->aux)
-        cudaStreamDestroy(ctx->aux);
     if (ctx->cpy)
         cudaStreamDestroy(ctx->cpy);
     for (uint32_t b = 0; b < ask_ctx::kMaxBands; ++b)
         if (ctx->band_ev[b])
             cudaEventDestroy(ctx->band_ev[b]);
-    if (ctx->fork_ev)
-        cudaEventDestroy(ctx->fork_ev);
-    if (ctx->join_ev)
-        cudaEventDestroy(ctx->join_ev);
     if (ctx->events)
         for (int i = 0; i < ASK_MAX_LEVELS + 4; ++i)
             cudaEventDestroy(ctx->ev[i]);
@@ -1201,7 +1153,7 @@ ask_status ask_timing_read(ask_ctx *ctx, void *stream, ask_timing *out)
             }
             cudaEventElapsedTime(&ms, sl.ev[L + 1], sl.ev[L + 2]);
             out->ms_fill += ms;
-            cudaEventElapsedTime(&ms, sl.ev[L + 1], sl.ev[L + 3]);
+            cudaEventElapsedTime(&ms, sl.ev[L + 2], sl.ev[L + 3]);
             out->ms_leaf += ms;
         }
         out->levels = L;
@@ -1257,6 +1209,7 @@ ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nfra
         }
         stats->leaves = c.leaf_count;
         stats->fill_pixels = c.fill_pixels;
+        stats->deferred_fill_pixels = c.deferred_fill_pixels;
         stats->leaf_pixels = c.leaf_pixels;
         stats->border_pixels = c.border_pixels;
         stats->iterations = c.iterations;

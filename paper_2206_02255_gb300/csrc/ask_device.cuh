@@ -262,6 +262,33 @@ __device__ __forceinline__ void fill_rect(uint32_t *__restrict__ map, uint32_t n
     }
 }
 
+// Warp fill of a band of the deferred-fill list.  Rows of at least 128
+// pixels go one at a time, the lanes striding over the row's whole 16-byte
+// chunks (one 128-bit store, a pointer step and a compare each), with the at
+// most 3 + 3 pixels outside them stored singly; narrower bands use fill_rect.
+__device__ __forceinline__ void fill_band_warp(uint32_t *__restrict__ map, uint32_t n,
+                                               const Region &g, uint32_t v, uint32_t lane)
+{
+    if (g.w < 128u) {
+        fill_rect(map, n, g, v, lane, 32u);
+        return;
+    }
+    const uint4 v4 = make_uint4(v, v, v, v);
+    for (uint32_t row = 0; row < g.h; ++row) {
+        const size_t start = (size_t)(g.y0 + row) * n + g.x0;
+        const size_t end = start + g.w;
+        const size_t a4 = (start + 3u) >> 2, b4 = end >> 2;  // whole chunks [a4, b4)
+        uint4 *q = reinterpret_cast<uint4 *>(map) + a4 + lane;
+        uint4 *const qe = reinterpret_cast<uint4 *>(map) + b4;
+        for (; q < qe; q += 32)
+            *q = v4;
+        if (lane < 3u && start + lane < (a4 << 2))
+            map[start + lane] = v;
+        if (lane >= 3u && lane < 6u && (b4 << 2) + (lane - 3u) < end)
+            map[(b4 << 2) + (lane - 3u)] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Perimeter uniformity queries for regions that split when not uniform.
 //

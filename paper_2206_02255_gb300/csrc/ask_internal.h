@@ -28,6 +28,7 @@ struct DevCounters {
     unsigned long long border_pixels;       // COUNT mode
     unsigned long long level_iters[ASK_MAX_LEVELS];  // COUNT mode: z-updates of level i
     unsigned long long leaf_iters;          // COUNT mode: z-updates of the leaf kernel
+    unsigned long long deferred_fill_pixels; // COUNT mode: pixels of the deferred-fill list
     uint32_t work[ASK_MAX_LEVELS];          // next work item a level kernel hands out
     uint32_t leaf_work;                     // next leaf the leaf kernel hands out
     uint32_t fill_count;                    // entries in the deferred-fill list
@@ -120,19 +121,31 @@ constexpr uint32_t kChunkPx = 64;
 constexpr uint32_t kChunkPxBatch = 128;
 // Uniform regions larger than this are filled by the fill kernel.
 constexpr uint32_t kInPlaceFillArea = 16384;
+// The fill kernel's list holds bands of whole rows of a uniform region, at
+// most kFillBandPx pixels each (one row if the region is wider), so its work
+// items are of near-equal size whatever the regions' sizes.
+constexpr uint32_t kFillBandPx = 16384;
+__host__ __device__ inline uint32_t fill_band_rows(uint32_t w)
+{
+    return w >= kFillBandPx ? 1u : kFillBandPx / w;
+}
+__host__ __device__ inline uint32_t fill_band_count(uint32_t w, uint32_t h)
+{
+    const uint32_t rows = fill_band_rows(w);
+    return h / rows + (h % rows != 0u);
+}
 cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cudaStream_t s);
 
 struct FillArgs {
     uint32_t *map;        // single frame (batch entries name their frame)
     uint32_t n;
-    const uint4 *fills;
+    const uint4 *fills;   // bands (origin, extent, dwell, frame)
     uint32_t fill_cap;
-    uint32_t max_rows;    // largest height of a deferred region
     const FrameDesc *frames;
     DevCounters *ctr;
 };
-// grid <= 0: one resident wave over all SMs; else that many CTAs.
-cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, int grid, cudaStream_t s);
+// One resident wave of 256-thread CTAs over all SMs.
+cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, cudaStream_t s);
 cudaError_t launch_init_batch(uint4 *olt0, uint4 *rst0, DevCounters *ctr, const FrameDesc *frames,
                               uint32_t nframes, uint32_t total0, cudaStream_t s);
 
@@ -147,6 +160,8 @@ struct LeafArgs {
     const void *leaves;   // uint2 (single frame) or uint4 (batch) records
     uint32_t leaf_cap;    // capacity of the leaf list
     uint32_t skip_perimeter;  // leaf perimeters are already in the map
+    const uint4 *fills;   // lane-refill kernel: deferred-fill bands to write
+    uint32_t fill_cap;    //   along the way (NULL: none)
     const FrameDesc *frames;
     DevCounters *ctr;
 };

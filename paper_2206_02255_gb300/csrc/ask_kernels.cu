@@ -202,17 +202,30 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH>
                 atomicOr(&ctr->error, ERR_LEAF_OVERFLOW);
         }
     }
-    // large uniform regions for the fill kernel
+    // large uniform regions for the fill list, as bands of rows: a warp
+    // scan of the band counts, one atomicAdd, then each lane writes the
+    // bands of its region
     const unsigned later_mask = __ballot_sync(kFull, b.kind == KIND_FILL_LATER);
     if (later_mask) {
+        const Region g = R::region(b.rec);
+        const uint32_t nb = (b.kind == KIND_FILL_LATER) ? fill_band_count(g.w, g.h) : 0u;
+        uint32_t incl = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (uint32_t)o)
+                incl += v;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
         uint32_t base = 0;
         if (lane == 0)
-            base = atomicAdd(&ctr->fill_count, (uint32_t)__popc(later_mask));
-        base = __shfl_sync(kFull, base, 0);
-        if (b.kind == KIND_FILL_LATER) {
-            const uint32_t slot = base + (uint32_t)__popc(later_mask & lt);
-            if (slot < a.fill_cap)
-                a.fills[slot] = make_uint4(b.rec.x, b.rec.y, b.dwell, R::frame(b.rec));
+            base = atomicAdd(&ctr->fill_count, total);
+        base = __shfl_sync(kFull, base, 0) + incl - nb;
+        const uint32_t rows = fill_band_rows(g.w);
+        for (uint32_t j = 0; j < nb; ++j) {
+            const uint2 band = pack_region(g.x0, g.y0 + j * rows, g.w, min(rows, g.h - j * rows));
+            if (base + j < a.fill_cap)
+                a.fills[base + j] = make_uint4(band.x, band.y, b.dwell, R::frame(b.rec));
             else
                 atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
         }
@@ -398,7 +411,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
     b.dwell = 0;
     b.sc = b.r = 1u;
     uint32_t j = 0;
-    unsigned long long it = 0, bpx = 0, fpx = 0;
+    unsigned long long it = 0, bpx = 0, fpx = 0, dpx = 0;
 
     for (;;) {
         // items are handed out one at a time: their costs differ by orders
@@ -501,8 +514,11 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                     fill_rect(f.map, f.n, g, wv, lane, 32u);
                     kind = KIND_FILL;
                 }
-                if (COUNT && lane == 0)
+                if (COUNT && lane == 0) {
                     fpx += area;
+                    if (kind == KIND_FILL_LATER)
+                        dpx += area;
+                }
             } else {
                 kind = f.split ? KIND_SPLIT : KIND_LEAF;
             }
@@ -527,6 +543,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
         it = warp_sum_u64(it);
         bpx = warp_sum_u64(bpx);
         fpx = warp_sum_u64(fpx);
+        dpx = warp_sum_u64(dpx);
         if (lane == 0) {
             if (it) {
                 atomicAdd(&a.ctr->iterations, it);
@@ -536,40 +553,31 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                 atomicAdd(&a.ctr->border_pixels, bpx);
             if (fpx)
                 atomicAdd(&a.ctr->fill_pixels, fpx);
+            if (dpx)
+                atomicAdd(&a.ctr->deferred_fill_pixels, dpx);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Fill kernel: the large uniform regions, one row per warp item, 128-bit
-// stores; pure HBM writes spread over every SM.
+// Fill kernel: the bands of the large uniform regions (at most kFillBandPx
+// pixels each), one band per warp item, 128-bit stores; pure HBM writes.
 // ---------------------------------------------------------------------------
 template <bool BATCH>
 __global__ void __launch_bounds__(256) fill_kernel(FillArgs f)
 {
-    constexpr uint32_t kBand = 8;  // rows per work item
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nfill = min(f.ctr->fill_count, f.fill_cap);
-    const uint32_t bands = (f.max_rows + kBand - 1u) / kBand;
-    const unsigned long long total = (unsigned long long)nfill * bands;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long item = warp; item < total; item += nwarps) {
-        const uint32_t fi = (uint32_t)(item / bands);
-        const uint32_t band = (uint32_t)(item - (unsigned long long)fi * bands);
+    for (uint32_t fi = warp; fi < nfill; fi += nwarps) {
         const uint4 e = f.fills[fi];
         const Region g = unpack_region(make_uint2(e.x, e.y));
-        const uint32_t row = band * kBand;
-        if (row >= g.h)
-            continue;
-        Region rb = g;
-        rb.y0 = g.y0 + row;
-        rb.h = min(kBand, g.h - row);
         if (BATCH) {
             const FrameDesc &d = f.frames[e.w];
-            fill_rect(d.map, d.n, rb, e.z, lane, 32u);
+            fill_band_warp(d.map, d.n, g, e.z, lane);
         } else {
-            fill_rect(f.map, f.n, rb, e.z, lane, 32u);
+            fill_band_warp(f.map, f.n, g, e.z, lane);
         }
     }
 }
@@ -635,6 +643,12 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 //    written.
 // ---------------------------------------------------------------------------
 constexpr int kRefillWarps = 8;    // warps per CTA
+// Resident CTAs per SM: 5 for one frame (48 registers a thread; at 6 CTAs,
+// 40 registers, the refill loop spills once the fill warp's code is in the
+// kernel, and it measured slower), 4 for a batch (its per-frame lookups need
+// up to 64 registers).
+constexpr int kRefillMinBlocks = 5;
+constexpr int kRefillMinBlocksBatch = 4;
 constexpr uint32_t kParkCap = 128; // parked orbits per warp (< 32 + 2 * 32)
 constexpr int kLeafUnroll = 32;    // updates per unchecked block (a power of two)
 
@@ -716,6 +730,36 @@ __device__ __forceinline__ void finish_parked(const LeafArgs &a, float4 s, uint4
         it += d;
 }
 
+// Deferred fills ride along the leaf pass.  The last warp of every CTA
+// starts as a fill warp: it takes bands of the fill list (at most
+// kFillBandPx pixels each, 128-bit stores) from a counter until none are
+// left, then joins the leaf work; every warp that runs out of leaves helps
+// with the bands still left.  The HBM writes so proceed beside the FP32 work
+// of the other warps instead of in a kernel of their own (the bands and the
+// leaves are disjoint pixels), and the fill code sits outside the refill
+// loop, adding nothing to its registers.
+template <bool BATCH>
+__device__ __forceinline__ void drain_fills(const LeafArgs &a, uint32_t lane)
+{
+    const uint32_t nfill = min(a.ctr->fill_count, a.fill_cap);
+    for (;;) {
+        uint32_t fi = 0;
+        if (lane == 0)
+            fi = atomicAdd(&a.ctr->fill_work, 1u);
+        fi = __shfl_sync(kFull, fi, 0);
+        if (fi >= nfill)
+            return;
+        const uint4 e = a.fills[fi];
+        const Region g = unpack_region(make_uint2(e.x, e.y));
+        if (BATCH) {
+            const FrameDesc &d = a.frames[e.w];
+            fill_band_warp(d.map, d.n, g, e.z, lane);
+        } else {
+            fill_band_warp(a.map, a.n, g, e.z, lane);
+        }
+    }
+}
+
 // floor(q / w) for q < 2^22 given inv_w = 1/w rounded to float: (q + 1/2)/w
 // lies at least 1/(2w) away from an integer, far more than the rounding of
 // the two float operations, so truncation gives the exact quotient.
@@ -727,10 +771,14 @@ __device__ __forceinline__ uint32_t rows_in(uint32_t q, float inv_w)
 // One orbit slot of a lane.
 struct Slot {
     float x, y, cr, ci;
-    uint32_t d, pix, md;  // count, pixel (py << 16 | px), max_dwell of its frame
-    bool busy, fast;
+    uint32_t d, pix;  // count, pixel (py << 16 | px)
+    uint32_t lim;     // a whole unchecked block may run while d < lim
+    bool busy;
 };
 
+// lim = max_dwell - kLeafUnroll + 1 where escape is absorbing (the block
+// stays within max_dwell), else 0 (such points go straight to the tested
+// loop of finish_parked).
 __device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t md, uint32_t px,
                                            uint32_t py)
 {
@@ -741,8 +789,8 @@ __device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t
     o.y = 0.0f;
     o.d = 0;
     o.pix = (py << 16) | px;
-    o.md = md;
-    o.fast = escape_absorbing(c.x, c.y);
+    o.lim = (escape_absorbing(c.x, c.y) && md >= (uint32_t)kLeafUnroll) ? md - (uint32_t)kLeafUnroll + 1u
+                                                                         : 0u;
     o.busy = true;
 }
 
@@ -751,13 +799,16 @@ __device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t
 // chains interleave.  All lanes of a warp work on the same leaf (the same
 // frame) at a time; parked orbits remember their frame.
 template <bool COUNT, bool BATCH>
-__global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs a)
+__global__ void __launch_bounds__(kRefillWarps * 32, BATCH ? kRefillMinBlocksBatch : kRefillMinBlocks)
+    leaf_refill_kernel(LeafArgs a)
 {
     using R = Rec<BATCH>;
     using T = typename R::T;
     __shared__ float4 park_s[kRefillWarps][kParkCap];  // saved state at the block's start and midpoint
     __shared__ uint4 park_u[kRefillWarps][kParkCap];   // count, pixel, frame
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    if (a.fills != nullptr && wib == kRefillWarps - 1u)
+        drain_fills<BATCH>(a, lane);  // the CTA's fill warp
     const unsigned lt_mask = (1u << lane) - 1u;
     float4 *qs = park_s[wib];
     uint4 *qu = park_u[wib];
@@ -773,10 +824,9 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
     bool more = true;
     Slot s0, s1;
     s0.busy = s1.busy = false;
-    s0.fast = s1.fast = false;
     s0.x = s0.y = s0.cr = s0.ci = s1.x = s1.y = s1.cr = s1.ci = 0.0f;
     s0.d = s1.d = s0.pix = s1.pix = 0;
-    s0.md = s1.md = 0;
+    s0.lim = s1.lim = 0;
     uint32_t f0 = 0, f1 = 0;  // frames of the slots' orbits
     unsigned long long it = 0, lpx = 0;
 
@@ -815,7 +865,8 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                 continue;
             }
             const uint32_t n0 = (uint32_t)__popc(i0);
-            const uint32_t take = min(n0 + (uint32_t)__popc(i1), rem);
+            const uint32_t idle = n0 + (uint32_t)__popc(i1);
+            const uint32_t take = min(idle, rem);
             const uint32_t r0 = (uint32_t)__popc(i0 & lt_mask);
             const uint32_t r1 = n0 + (uint32_t)__popc(i1 & lt_mask);
             if (!s0.busy && r0 < take) {
@@ -834,10 +885,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
                 row0 += dr;
             }
             rem -= take;
+            if (take == idle)
+                break;  // every slot busy
             i0 = __ballot_sync(kFull, !s0.busy);
             i1 = __ballot_sync(kFull, !s1.busy);
         }
-        if (!__any_sync(kFull, s0.busy || s1.busy))
+        // slots stay idle only once the leaves have run out
+        if (!more && !__any_sync(kFull, s0.busy || s1.busy))
             break;
 
         // ---- one unchecked block on both slots (results of a slot that is
@@ -856,13 +910,13 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
         }
         bool park0 = false, park1 = false;
         if (s0.busy) {
-            if (s0.fast && s0.md - s0.d >= K && z_bounded(s0.x, s0.y))
+            if (s0.d < s0.lim && z_bounded(s0.x, s0.y))
                 s0.d += K;
             else
                 park0 = true;  // escaped in this block, tail below max_dwell, or |c| near 2
         }
         if (s1.busy) {
-            if (s1.fast && s1.md - s1.d >= K && z_bounded(s1.x, s1.y))
+            if (s1.d < s1.lim && z_bounded(s1.x, s1.y))
                 s1.d += K;
             else
                 park1 = true;
@@ -898,6 +952,8 @@ __global__ void __launch_bounds__(kRefillWarps * 32) leaf_refill_kernel(LeafArgs
             }
         }
     }
+    if (a.fills != nullptr)
+        drain_fills<BATCH>(a, lane);
     // ---- the orbits still parked
     if (lane < parked) {
         finish_parked<COUNT, BATCH>(a, qs[lane], qu[lane], it);
@@ -1009,15 +1065,13 @@ cudaError_t launch_level(const LevelArgs &a, bool count, bool batch, int sms, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, int grid, cudaStream_t s)
+cudaError_t launch_fill(const FillArgs &f, bool batch, int sms, cudaStream_t s)
 {
     if (batch) {
-        if (grid <= 0)
-            grid = persistent_grid(fill_kernel<true>, 256, 0, sms);
+        const int grid = persistent_grid(fill_kernel<true>, 256, 0, sms);
         fill_kernel<true><<<grid, 256, 0, s>>>(f);
     } else {
-        if (grid <= 0)
-            grid = persistent_grid(fill_kernel<false>, 256, 0, sms);
+        const int grid = persistent_grid(fill_kernel<false>, 256, 0, sms);
         fill_kernel<false><<<grid, 256, 0, s>>>(f);
     }
     return cudaGetLastError();

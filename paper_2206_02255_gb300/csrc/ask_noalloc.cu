@@ -241,6 +241,9 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
     la.leaves = sc->leaves;
     la.leaf_cap = kNoAllocRegions;
     la.skip_perimeter = 0u;
+    la.fills = nullptr;
+    la.fill_cap = 0u;
+    la.frames = nullptr;
     la.ctr = sc->ctr;
     if (launch_leaf(la, p.block_x, p.block_y, false, false, false, sc->sms, s) != cudaSuccess)
         return ASK_ECUDA;

@@ -70,13 +70,20 @@ __global__ void __launch_bounds__(1024) region_level_kernel(LevelArgs a)
             bpx += perimeter_size(g.w, g.h);
         if (uniform) {
             if (MBR) {
-                if (tid == 0) {
-                    const uint32_t slot = atomicAdd(&ctr->fill_count, 1u);
-                    if (slot < a.fill_cap)
-                        a.fills[slot] = make_uint4(e.x, e.y, wv, 0u);
+                // the region's bands of rows go to the fill list
+                const uint32_t nb = fill_band_count(g.w, g.h), rows = fill_band_rows(g.w);
+                if (tid == 0)
+                    s_base = atomicAdd(&ctr->fill_count, nb);
+                __syncthreads();
+                const uint32_t base = s_base;
+                for (uint32_t j = tid; j < nb; j += T) {
+                    const uint2 band = pack_region(g.x0, g.y0 + j * rows, g.w, min(rows, g.h - j * rows));
+                    if (base + j < a.fill_cap)
+                        a.fills[base + j] = make_uint4(band.x, band.y, wv, 0u);
                     else
                         atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
                 }
+                __syncthreads();
             } else {
                 fill_rect(a.map, a.n, g, wv, tid, T);
             }

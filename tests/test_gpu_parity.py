@@ -143,15 +143,49 @@ def test_ask_c0_counters(ctx, orc, asklib, exact):
     assert st["iterations"] == sum(st["iterations_per_level"]) + st["leaf_iterations"]
 
 
-@pytest.mark.parametrize("flags", ["EXACT_BORDERS", "LEAF_TILED", "EXACT_BORDERS|LEAF_TILED"])
+def test_ask_fill_rows_wider_than_a_band(ctx, orc, asklib):
+    """A window where every |c| > 2 is uniform (dwell 1) at level 0: with
+    g = 1 and n = 17000 the single region's rows are wider than one fill band
+    (16384 pixels), so the fill list holds one band per row."""
+    win, n, M = (2.5, 3.5, 2.5, 3.5), 17000, 64
+    want = orc.dwell(*orc.pixel_to_c(win, n, 0, 0), M)
+    assert want == 1
+    got, st = gpu_map(ctx, "ask", win, n, M, params(asklib, 1, 2, 16, count=True), stats=True)
+    assert int((got != want).sum()) == 0
+    assert st["fills_per_level"][0] == 1 and sum(st["regions_per_level"][1:]) == 0
+    assert st["deferred_fill_pixels"] == n * n
+
+
+def test_ask_deferred_fill_pixels(ctx, orc, asklib):
+    """Uniform regions of more than 16384 pixels are left to the fill kernel;
+    the counting render reports their pixels, which must be the area of the
+    reference's filled regions above that size."""
+    win, n, M, g, r, B = inputs.WINDOW_PAPER, 2048, 1024, 4, 4, 16
+    want, ost, log = orc.render_ms(win, n, M, g, r, B, log=True)
+    got, st = gpu_map(ctx, "ask", win, n, M, params(asklib, g, r, B, count=True), stats=True)
+    assert np.array_equal(got, want)
+    big = sum(int(e["w"]) * int(e["h"]) for e in log
+              if e["kind"] == 0 and int(e["w"]) * int(e["h"]) > 16384)
+    assert big > 0
+    assert st["deferred_fill_pixels"] == big
+    assert st["fill_pixels"] == ost["fill_pixels"]
+
+
+@pytest.mark.parametrize("flags", ["EXACT_BORDERS", "LEAF_TILED", "EXACT_BORDERS|LEAF_TILED",
+                                   "SERIAL_FILL", "SERIAL_FILL|EXACT_BORDERS"])
 def test_ask_flag_variants(ctx, orc, asklib, flags):
-    """The last-level and leaf-kernel variants give the same map."""
+    """The last-level, leaf-kernel and fill-schedule variants give the same
+    map (the last three cases have uniform regions above the in-place fill
+    size, some of them ragged)."""
     f = 0
     for name in flags.split("|"):
         f |= getattr(asklib, "FLAG_" + name)
     for win, n, M, g, r, B, block in [(inputs.WINDOW_PAPER, 1024, 512, 16, 2, 32, (16, 16)),
                                       (inputs.WINDOW_WIDE, 777, 300, 5, 3, 4, (8, 8)),
-                                      (inputs.WINDOW_PAPER, 2048, 2048, 32, 4, 16, (32, 8))]:
+                                      (inputs.WINDOW_PAPER, 2048, 2048, 32, 4, 16, (32, 8)),
+                                      (inputs.WINDOW_PAPER, 2048, 1024, 2, 4, 16, (16, 16)),
+                                      (inputs.WINDOW_WIDE, 3001, 700, 2, 2, 8, (16, 16)),
+                                      (inputs.WINDOW_WIDE, 2500, 400, 3, 5, 16, (16, 16))]:
         want, _ = orc.render_ms(win, n, M, g, r, B)
         p = params(asklib, g, r, B, block)
         p.flags = f
@@ -398,7 +432,7 @@ def test_invalid_arguments(ctx, asklib):
         (A, W, 8, 100, params(asklib, g=2, B=2), ptr + 4),      # not 16-byte aligned
         (E, W, 8, 100, params(asklib), ptr + 8),
     ]
-    for f in (0x100, asklib.FLAG_SBR | asklib.FLAG_MBR,
+    for f in (0x10000, asklib.FLAG_SBR | asklib.FLAG_MBR,
               asklib.FLAG_SBR | asklib.FLAG_EXACT_BORDERS, asklib.FLAG_MBR | asklib.FLAG_LEAF_TILED):
         flags_bad = params(asklib)
         flags_bad.flags = f
