@@ -689,23 +689,31 @@ def run_serve(args):
 
     # both paths share one pinned-buffer pool; results are released when
     # delivered.  Warm up (allocator caches, pinned buffers, first launches).
-    pool = serve.PinnedPool()
-    srv = serve.Server(device=local, slots=2, budget_bytes=40 * 2 ** 30, pool=pool, keep=False)
+    pool, dpool = serve.PinnedPool(), serve.DevicePool(local)
+    srv = serve.Server(device=local, slots=2, budget_bytes=40 * 2 ** 30, pool=pool, keep=False,
+                       dpool=dpool)
     srv.run(fresh(reqs[:64], at_zero=True))
-    serve.serve_per_frame(ctx, fresh(reqs[:64], at_zero=True), pool=pool, keep=False)
+    serve.serve_per_frame(ctx, fresh(reqs[:64], at_zero=True), pool=pool, keep=False, dpool=dpool)
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
     served = serve.summarize(srv.run(fresh(reqs)))
     clk = clocks.stop()
-    alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs), pool=pool, keep=False))
+    alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs), pool=pool, keep=False,
+                                                  dpool=dpool))
     # saturation: the first 600 requests all waiting at t = 0.  One untimed
-    # pass first fills the pinned pool to the depth a full batch needs (a
-    # server in steady state holds it; pinning memory on demand is slow).
+    # pass first fills the buffer pools to the depth full batches need (a
+    # server in steady state holds them; allocating on demand is slow).
+    # Three passes of each; the median pass is reported (the batches a
+    # saturated server forms depend on host timing, so passes differ).
     srv.run(fresh(reqs[:600], at_zero=True))
-    sat_served = serve.summarize(srv.run(fresh(reqs[:600], at_zero=True)))
-    sat_alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs[:600], at_zero=True), pool=pool,
-                                                      keep=False))
+    sat_s = sorted((serve.summarize(srv.run(fresh(reqs[:600], at_zero=True))) for _ in range(3)),
+                   key=lambda r: r["gpix_s"])
+    sat_a = sorted((serve.summarize(serve.serve_per_frame(ctx, fresh(reqs[:600], at_zero=True),
+                                                          pool=pool, keep=False, dpool=dpool))
+                    for _ in range(3)),
+                   key=lambda r: r["gpix_s"])
+    sat_served, sat_alone = sat_s[1], sat_a[1]
     srv.close()
     px = float(sum(d["n"] * d["n"] for d in reqs))
     value = whole_job_rate(world, px, served["span_s"], dev) / 1e9
@@ -724,7 +732,10 @@ def run_serve(args):
             "saturated_600": {"served_gpix_s": sat_served["gpix_s"],
                               "per_frame_gpix_s": sat_alone["gpix_s"],
                               "served_p99_ms": sat_served["p99_ms"],
-                              "per_frame_p99_ms": sat_alone["p99_ms"]},
+                              "per_frame_p99_ms": sat_alone["p99_ms"],
+                              "passes": 3, "reported": "median pass",
+                              "served_gpix_s_all": [r["gpix_s"] for r in sat_s],
+                              "per_frame_gpix_s_all": [r["gpix_s"] for r in sat_a]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(4 * px), "note": "latency includes the D2H copy"},
             "clocks": clk,

@@ -39,9 +39,33 @@ class PinnedPool:
         self.free.setdefault(buf.numel(), []).append(buf)
 
 
+class DevicePool:
+    """Device dwell buffers by power-of-two size class, reused across
+    requests like the pinned pool: in steady state a server allocates
+    nothing, so no allocation (and the device synchronisation that
+    cudaMalloc can bring) falls inside a batch's lifetime.  Class sizes are
+    multiples of 4 KiB, so every view starts 16-byte aligned."""
+
+    def __init__(self, device=0):
+        self.device = device
+        self.free = {}
+
+    def get(self, n):
+        import torch
+        nbytes = 4 * n * n
+        cls = 1 << max(12, (nbytes - 1).bit_length())
+        lst = self.free.get(cls)
+        buf = lst.pop() if lst else torch.empty(cls, dtype=torch.uint8,
+                                                device="cuda:%d" % self.device)
+        return buf, buf[:nbytes].view(torch.int32).view(n, n)
+
+    def put(self, buf):
+        self.free.setdefault(buf.numel(), []).append(buf)
+
+
 class Request:
     __slots__ = ("id", "t", "window", "n", "max_dwell", "g", "r", "B", "out", "host",
-                 "hbuf", "t_done", "event")
+                 "hbuf", "dbuf", "t_done", "event")
 
     def __init__(self, d, g, r, B):
         self.id = d["id"]
@@ -50,7 +74,7 @@ class Request:
         self.n = d["n"]
         self.max_dwell = d["max_dwell"]
         self.g, self.r, self.B = g, r, B
-        self.out = self.host = self.hbuf = self.event = None
+        self.out = self.host = self.hbuf = self.dbuf = self.event = None
         self.t_done = None
 
     @property
@@ -71,10 +95,11 @@ class Server:
     """Continuous-batching server over `slots` contexts on one device."""
 
     def __init__(self, device=0, slots=2, budget_bytes=40 * 2 ** 30, max_frames=256, pool=None,
-                 keep=True):
+                 keep=True, dpool=None):
         import torch
         self.device = device
         self.pool = pool if pool is not None else PinnedPool()
+        self.dpool = dpool if dpool is not None else DevicePool(device)
         self.keep = keep  # keep results on the requests; else recycle at completion
         self.budget = budget_bytes
         self.max_frames = max_frames
@@ -92,7 +117,7 @@ class Server:
         s = self.streams[slot]
         with torch.cuda.stream(s):
             for q in reqs:
-                q.out = torch.empty((q.n, q.n), dtype=torch.int32, device="cuda:%d" % self.device)
+                q.dbuf, q.out = self.dpool.get(q.n)
                 q.hbuf, q.host = self.pool.get(q.n)
             frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r, B=q.B,
                            out=q.out) for q in reqs]
@@ -124,7 +149,8 @@ class Server:
                     for q in reqs:
                         q.t_done = tn
                         self.used -= q.nbytes
-                        q.out = None
+                        self.dpool.put(q.dbuf)
+                        q.out = q.dbuf = None
                         if not self.keep:
                             self.pool.put(q.hbuf)
                             q.hbuf = q.host = None
@@ -152,25 +178,27 @@ class Server:
         return requests
 
 
-def serve_per_frame(ctx, requests, poll_s=0.0002, pool=None, keep=True):
+def serve_per_frame(ctx, requests, poll_s=0.0002, pool=None, keep=True, dpool=None):
     """Baseline: one request at a time in arrival order, single-frame ASK,
     map copied to pinned host memory; returns requests with t_done set."""
     import torch
     pool = pool if pool is not None else PinnedPool()
+    dpool = dpool if dpool is not None else DevicePool(ctx.device)
     s = torch.cuda.Stream(device=ctx.device)
     t0 = time.perf_counter()
     for q in requests:
         while time.perf_counter() - t0 < q.t:
             time.sleep(poll_s)
         with torch.cuda.stream(s):
-            q.out = torch.empty((q.n, q.n), dtype=torch.int32, device="cuda:%d" % ctx.device)
+            q.dbuf, q.out = dpool.get(q.n)
             q.hbuf, q.host = pool.get(q.n)
             ctx.render("ask", q.window, q.n, q.max_dwell, ask.make_params(q.g, q.r, q.B),
                        out=q.out, stream=s)
             q.host.copy_(q.out, non_blocking=True)
         s.synchronize()
         q.t_done = time.perf_counter() - t0
-        q.out = None
+        dpool.put(q.dbuf)
+        q.out = q.dbuf = None
         if not keep:
             pool.put(q.hbuf)
             q.hbuf = q.host = None
