@@ -477,9 +477,12 @@ def run_gpu(args):
         ctx.render_host("ask", win, n, M, ask.make_params(g, r, B, blk), out=host)
         k_e2e = max(3, args.steps // 2)
         barrier(world)
+        calls = []
         t0 = time.perf_counter()
         for _ in range(k_e2e):
+            tc = time.perf_counter()
             ctx.render_host("ask", win, n, M, ask.make_params(g, r, B, blk), out=host)
+            calls.append(1e3 * (time.perf_counter() - tc))
         t_e2e = (time.perf_counter() - t0) / k_e2e
         t_e2e = max_over_ranks(world, t_e2e, dev)
         # the same call with the map rendered in device memory and copied after
@@ -492,7 +495,7 @@ def run_gpu(args):
         e2e = {"value": world * pixels / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": int(pixels * 4), "ms_per_step": 1e3 * t_e2e,
                "path": "banded: each band of initial-region rows is copied while the next renders",
-               "staged_copy_ms_per_step": 1e3 * t_staged}
+               "ms_per_call": calls, "staged_copy_ms_per_step": 1e3 * t_staged}
         del host
 
     # ---- CPU reference on a bounded sample (rank 0, N = 1) -----------------
