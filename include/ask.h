@@ -108,6 +108,12 @@ typedef enum {
  * second stream); the same map.  With ASK_FLAG_TIMING this times the fill
  * kernel by itself. */
 #define ASK_FLAG_SERIAL_FILL 256u
+/* ASK, fault injection for tests of error reporting: the kernels see region
+ * tables of capacity 1 (the allocations keep their size, nothing is written
+ * out of bounds), so a render that needs more latches a capacity overflow:
+ * the next synchronising call returns ASK_EOVERFLOW and clears it.  The map
+ * of such a render is incomplete. */
+#define ASK_FLAG_INJECT_OVERFLOW 512u
 
 typedef struct {
     float re_min, re_max, im_min, im_max;

@@ -123,17 +123,27 @@ class BatchTuner:
         del scratch
         return self
 
+    # Largest initial-region side given to a frame of a batch: a batch splits
+    # every region of a level into as many chunks as its largest region
+    # needs (up to a cap), so a few huge regions cost every frame work items.
+    MAX_S0 = 512
+
     def choose(self, frame):
-        """(g, r, B) of the nearest probe (log n, log dwell cap, log zoom)."""
+        """(g, r, B) of the nearest probe (log n, log dwell cap, log zoom).
+        The probe's initial-region side s0 = ceil(n / g) carries over, not its
+        g, so frames larger or smaller than the probe get regions of the same
+        size; s0 is kept at most MAX_S0."""
         key = self._key(frame)
         best = None
         for f, cfg, _ in self.probes:
             pk = self._key(f)
             dist = abs(key[0] - pk[0]) + abs(key[1] - pk[1]) + 0.5 * abs(key[2] - pk[2])
             if best is None or dist < best[0]:
-                best = (dist, cfg)
-        cfg = best[1]
-        g = min(cfg["g"], frame["n"])
+                best = (dist, f, cfg)
+        _, f, cfg = best
+        n = frame["n"]
+        s0 = min(-(-f["n"] // cfg["g"]), self.MAX_S0)
+        g = max(1, min(-(-n // s0), n, max(DEFAULT_SPACE["g"])))
         return g, cfg["r"], cfg["B"]
 
     def summary(self):

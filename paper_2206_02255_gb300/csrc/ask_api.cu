@@ -205,7 +205,7 @@ ask_status check_args(ask_ctx *ctx, ask_method method, const ask_window *window,
         return set_err(ctx, ASK_EINVAL, "block_x * block_y must be a multiple of 32 in [32, 1024]");
     if (d.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_TIMING | ASK_FLAG_CDP2_FIRE_AND_FORGET |
                     ASK_FLAG_EXACT_BORDERS | ASK_FLAG_LEAF_TILED | ASK_FLAG_SBR | ASK_FLAG_MBR |
-                    ASK_FLAG_STAGED_COPY | ASK_FLAG_SERIAL_FILL))
+                    ASK_FLAG_STAGED_COPY | ASK_FLAG_SERIAL_FILL | ASK_FLAG_INJECT_OVERFLOW))
         return set_err(ctx, ASK_EINVAL, "unknown flags 0x%x", d.flags);
     if ((d.flags & ASK_FLAG_SBR) && (d.flags & ASK_FLAG_MBR))
         return set_err(ctx, ASK_EINVAL, "ASK_FLAG_SBR and ASK_FLAG_MBR exclude each other");
@@ -556,6 +556,12 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     const int sms = ctx->dev.sms;
     const uint32_t L = plan.levels;
     const bool exact = (p.flags & ASK_FLAG_EXACT_BORDERS) != 0;
+    // ASK_FLAG_INJECT_OVERFLOW: the kernels see region tables of capacity 1
+    // (the allocations keep their full size, so nothing is written out of
+    // bounds) and latch the overflow, as a real one would be.
+    const bool inject = (p.flags & ASK_FLAG_INJECT_OVERFLOW) != 0;
+    const uint32_t olt_cap = inject ? 1u : (uint32_t)ctx->olt_cap;
+    const uint32_t leaf_cap = inject ? 1u : (uint32_t)ctx->leaf_cap;
     mk.at(0, s);
     if (row0 >= plan.axis0)
         return set_err(ctx, ASK_EINVAL, "band starts past the last initial-region row");
@@ -578,13 +584,13 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.r = p.r;
         a.olt_in = ctx->olt[i & 1];
         a.olt_out = ctx->olt[(i + 1) & 1];
-        a.olt_cap = (uint32_t)ctx->olt_cap;
+        a.olt_cap = olt_cap;
         a.chunks = plan.chunks[i];
         a.next_chunks = (i + 1 < L) ? plan.chunks[i + 1] : 1u;
         a.rst_in = ctx->rst[i & 1];
         a.rst_out = ctx->rst[(i + 1) & 1];
         a.leaves = ctx->leaves;
-        a.leaf_cap = (uint32_t)ctx->leaf_cap;
+        a.leaf_cap = leaf_cap;
         a.fills = ctx->fill_cap ? ctx->fills : nullptr;
         a.fill_cap = (uint32_t)ctx->fill_cap;
         a.exact_last = exact ? 1u : 0u;
@@ -626,7 +632,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     la.max_dwell = max_dwell;
     la.side = plan.side[L - 1];
     la.leaves = ctx->leaves;
-    la.leaf_cap = (uint32_t)ctx->leaf_cap;
+    la.leaf_cap = leaf_cap;
     la.skip_perimeter = exact ? 1u : 0u;
     la.fills = fused ? ctx->fills : nullptr;
     la.fill_cap = fused ? (uint32_t)ctx->fill_cap : 0u;
@@ -738,6 +744,7 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
             bp.L = plan.levels;
     }
     for (uint32_t i = 0; i < bp.L; ++i) {
+        bp.chunks[i] = std::min(bp.chunks[i], kMaxChunksBatch);
         if (level_regions[i] * bp.chunks[i] >= 0xffffffffull)
             return set_err(ctx, ASK_EINVAL, "batch too large: level %u holds too many work items", i);
         if (level_regions[i] > bp.olt_need)

@@ -119,6 +119,12 @@ struct LevelArgs {
 // regions enough, and there a chunk's fixed cost weighs more.
 constexpr uint32_t kChunkPx = 64;
 constexpr uint32_t kChunkPxBatch = 128;
+// A batch splits every region of a level into the same number of chunks (the
+// work items are region x chunk), at most kMaxChunksBatch; a region whose
+// perimeter exceeds that many kChunkPxBatch chunks takes longer chunks.  The
+// cap keeps one frame with huge regions from multiplying the work items of
+// every other frame.
+constexpr uint32_t kMaxChunksBatch = 8;
 // Uniform regions larger than this are filled by the fill kernel.
 constexpr uint32_t kInPlaceFillArea = 16384;
 // The fill kernel's list holds bands of whole rows of a uniform region, at

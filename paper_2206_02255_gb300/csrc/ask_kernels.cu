@@ -471,7 +471,9 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
         } else {
             const uint32_t c = t - region * chunks;
             uint4 *st = a.rst_in + region;
-            constexpr uint32_t CP = BATCH ? kChunkPxBatch : kChunkPx;
+            // one frame: chunks cover the level's largest perimeter; a batch
+            // caps the chunk count, so a large region takes longer chunks
+            const uint32_t CP = BATCH ? max(kChunkPxBatch, ceil_div_u32(P, chunks)) : kChunkPx;
             const uint32_t k0 = min(P, c * CP), k1 = min(P, k0 + CP);
             if (COUNT && lane == 0)
                 bpx += k1 - k0;

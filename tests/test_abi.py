@@ -24,6 +24,20 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def test_binding_constants_match_the_header(asklib):
+    """Every ASK_FLAG_* and ask_status value of the header has the same
+    value in the Python binding."""
+    text = open(os.path.join(ROOT, "include", "ask.h")).read()
+    flags = dict(re.findall(r"#define\s+ASK_(FLAG_[A-Z0-9_]+)\s+(\d+)u", text))
+    assert len(flags) >= 10
+    for name, v in flags.items():
+        assert getattr(asklib, name) == int(v), name
+    statuses = re.findall(r"ASK_(E[A-Z]+|OK)\s*=\s*(\d+)", text)
+    assert len(statuses) == 8
+    for name, v in statuses:
+        assert getattr(asklib, name) == int(v), name
+
+
 def test_library_exports_every_declared_symbol(asklib):
     lib = ctypes.CDLL(asklib.lib_path())
     for name in declared_functions():

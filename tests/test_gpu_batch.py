@@ -29,6 +29,9 @@ MIXED = [
     (inputs.WINDOW_PAPER, 2048, 2048, 32, 4, 16),
     ((-1.9, 0.6, -0.3, 1.2), 1000, 1, 5, 3, 16),
     ((0.25, 0.26, -0.005, 0.005), 777, 3000, 2, 2, 8),
+    # one initial region with an 11996-pixel perimeter: more chunks than a
+    # batch level takes, so its chunks are longer than the others'
+    (inputs.WINDOW_WIDE, 3000, 300, 1, 2, 16),
 ]
 
 

@@ -156,6 +156,23 @@ def test_ask_fill_rows_wider_than_a_band(ctx, orc, asklib):
     assert st["deferred_fill_pixels"] == n * n
 
 
+@pytest.mark.parametrize("n,g", [(2049, 2), (1027, 1), (4099, 3), (520, 1), (259, 2), (255, 1)])
+def test_ask_fill_band_edges(ctx, orc, asklib, n, g):
+    """Uniform windows (every |c| > 2, dwell 1) whose level-0 regions go to
+    the fill list: odd n puts row starts and region origins off 16-byte
+    boundaries, and the widths run from just above the 128 pixels where a
+    band's rows are written one at a time (n = 259, g = 2: widths 130 and
+    129) to several bands per region (n = 2049, g = 2: 1025 and 1024;
+    n = 4099, g = 3: 1367 and 1365).  The map must be all ones, and every
+    pixel must come from a deferred fill."""
+    win, M = (2.5, 3.5, 2.5, 3.5), 64
+    assert orc.dwell(*orc.pixel_to_c(win, n, n - 1, n - 1), M) == 1
+    got, st = gpu_map(ctx, "ask", win, n, M, params(asklib, g, 2, 16, count=True), stats=True)
+    assert int((got != 1).sum()) == 0
+    assert st["fill_pixels"] == n * n and st["leaf_pixels"] == 0
+    assert st["deferred_fill_pixels"] == n * n
+
+
 def test_ask_deferred_fill_pixels(ctx, orc, asklib):
     """Uniform regions of more than 16384 pixels are left to the fill kernel;
     the counting render reports their pixels, which must be the area of the
@@ -398,6 +415,48 @@ def _raw_render(ctx, asklib, method, win, n, M, p, ptr):
     return lib().ask_render(ctx.handle, method, ctypes.byref(Window(*win)), n, M,
                             ctypes.byref(p) if p is not None else None, ctypes.c_void_p(ptr),
                             None, None)
+
+
+def test_injected_overflow_is_reported_and_cleared(ctx, orc, asklib):
+    """Fault injection through the ABI: with ASK_FLAG_INJECT_OVERFLOW the
+    kernels see region tables of capacity 1.  The overflow is latched on the
+    device and reported by the next synchronising call (a render with stats,
+    or ask_check after an asynchronous render), which clears it; the context
+    then renders correctly again."""
+    C = inputs.C0
+    win, n, M, g, r, B = C["window"], C["n"], C["max_dwell"], C["g"], C["r"], C["B"]
+    bad = params(asklib, g, r, B)
+    bad.flags = asklib.FLAG_INJECT_OVERFLOW
+    with pytest.raises(asklib.AskError) as ei:
+        gpu_map(ctx, "ask", win, n, M, bad, stats=True)
+    assert ei.value.status == asklib.EOVERFLOW
+    want, _ = orc.render_ms(win, n, M, g, r, B)
+    got, st = gpu_map(ctx, "ask", win, n, M, params(asklib, g, r, B), stats=True)
+    assert first_diff(got, want) is None
+    ctx.render("ask", win, n, M, bad)  # asynchronous: nothing to report yet
+    with pytest.raises(asklib.AskError) as ei:
+        ctx.check()
+    assert ei.value.status == asklib.EOVERFLOW
+    ctx.check()  # cleared
+    got = gpu_map(ctx, "ask", win, n, M, params(asklib, g, r, B))
+    assert first_diff(got, want) is None
+
+
+@pytest.mark.parametrize("method", ["ask", "exhaustive", "cdp2"])
+def test_no_write_outside_the_map(ctx, asklib, method):
+    """Guard bands before and after the n*n output keep their sentinel: no
+    kernel writes outside the map (ragged n puts row ends off 16-byte
+    boundaries; the window makes fills, splits and leaves)."""
+    import torch
+    pre, post, sentinel = 1024, 4096, 0x5A5A5A5A
+    for n, g in ((1, 1), (3, 2), (37, 3), (517, 4), (1031, 2), (2053, 3)):
+        buf = torch.full((pre + n * n + post,), sentinel, dtype=torch.int32, device="cuda")
+        out = buf[pre:pre + n * n].view(n, n)
+        ctx.render(method, inputs.WINDOW_WIDE, n, 300, params(asklib, g, 2, 8), out=out)
+        torch.cuda.synchronize()
+        assert int((buf[:pre] != sentinel).sum()) == 0, (method, n)
+        assert int((buf[pre + n * n:] != sentinel).sum()) == 0, (method, n)
+        assert int((out == sentinel).sum()) == 0, (method, n)
 
 
 def test_invalid_arguments(ctx, asklib):
