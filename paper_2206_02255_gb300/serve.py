@@ -2,14 +2,15 @@
 
 Requests (window, n, dwell cap) arrive over time.  The server keeps a queue
 of arrived requests and a fixed number of batch slots, each a context (its
-own region tables on the device) with its own CUDA stream.  Whenever a slot
+own region tables on the device) with its own copy stream.  Whenever a slot
 is free it admits queued requests, oldest first, while their dwell buffers
 fit in the memory budget, and renders them as one batch (one launch chain
-for every frame of the batch, region queues on the device); the maps are
-then copied to pinned host memory on the same stream.  Requests that arrive
-while batches run wait for the next free slot, so the work of consecutive
-batches overlaps on the device.  A request's latency runs from its arrival
-to the moment its map is in host memory.
+for every frame of the batch, region queues on the device).  Batches render
+one after another on one compute stream, since each launch chain fills the
+whole GPU; the maps of a batch are copied to pinned host memory on its
+slot's copy stream while the next batch renders.  Requests that arrive
+while batches run wait for the next free slot.  A request's latency runs
+from its arrival to the moment its map is in host memory.
 
 The baseline, :func:`serve_per_frame`, renders the same requests one at a
 time, in arrival order, with the single-frame ASK call.
@@ -104,7 +105,8 @@ class Server:
         self.budget = budget_bytes
         self.max_frames = max_frames
         self.ctxs = [ask.Context(device) for _ in range(slots)]
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self.compute = torch.cuda.Stream(device=device)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]  # copies
         self.busy = [None] * slots       # list of requests in flight per slot
         self.used = 0                    # bytes of dwell buffers in flight
 
@@ -114,14 +116,18 @@ class Server:
 
     def _start(self, slot, reqs):
         import torch
-        s = self.streams[slot]
-        with torch.cuda.stream(s):
+        c, s = self.compute, self.streams[slot]
+        with torch.cuda.stream(c):
             for q in reqs:
                 q.dbuf, q.out = self.dpool.get(q.n)
                 q.hbuf, q.host = self.pool.get(q.n)
             frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r, B=q.B,
                            out=q.out) for q in reqs]
-            self.ctxs[slot].render_batch(frames, stream=s)
+            self.ctxs[slot].render_batch(frames, stream=c)
+            rendered = torch.cuda.Event()
+            rendered.record(c)
+        s.wait_event(rendered)
+        with torch.cuda.stream(s):
             for q in reqs:
                 q.host.copy_(q.out, non_blocking=True)
             ev = torch.cuda.Event()
