@@ -103,9 +103,10 @@ typedef enum {
 #define ASK_FLAG_MBR 64u
 /* ask_render_host: render the whole map, then copy it (no banded pipeline). */
 #define ASK_FLAG_STAGED_COPY 128u
-/* ASK: run the deferred-fill kernel alone, on the render stream before the
- * leaf kernel, over every SM (by default it runs beside the leaf kernel on a
- * second stream); the same map.  With ASK_FLAG_TIMING this times the fill
+/* ASK: write the deferred fills (uniform regions of more than 16384 pixels)
+ * with the fill kernel alone, on the render stream before the leaf kernel,
+ * over every SM; by default the leaf kernel's fill warps write them beside
+ * its FP32 work.  The same map.  With ASK_FLAG_TIMING this times the fill
  * kernel by itself. */
 #define ASK_FLAG_SERIAL_FILL 256u
 /* ASK, fault injection for tests of error reporting: the kernels see region
@@ -143,16 +144,15 @@ typedef struct {
     uint64_t leaf_iterations;                  /* ASK_FLAG_COUNT, ASK: z-updates of the leaf kernel */
     float ms_total;                            /* device time of the render */
     float ms_per_level[ASK_MAX_LEVELS];        /* ASK: device time of level kernel i */
-    float ms_leaf;                             /* ASK: leaf kernel, from the end of the levels
-                                                * (from the end of the fill kernel when that
-                                                * runs first: ASK_FLAG_SERIAL_FILL, MBR) */
-    float ms_fill;                             /* ASK: deferred-fill kernel, from the end of the
-                                                * levels (by default it runs beside the leaf
-                                                * kernel) */
+    float ms_leaf;                             /* ASK: leaf kernel (by default with the
+                                                * deferred fills), after the fill kernel when
+                                                * that runs (ASK_FLAG_SERIAL_FILL, tiled leaf,
+                                                * MBR) */
+    float ms_fill;                             /* ASK: the fill kernel when it runs, else ~0 */
     uint32_t kernel_launches;                  /* kernels this render launched from the host */
     uint32_t pad2_;
     uint64_t deferred_fill_pixels;             /* ASK_FLAG_COUNT, ASK: pixels of the uniform
-                                                * regions left to the deferred-fill kernel */
+                                                * regions left to the deferred fills */
 } ask_stats;
 
 /* Per-kernel device time summed over the renders made with ASK_FLAG_TIMING

@@ -31,8 +31,8 @@ struct DevCounters {
     unsigned long long deferred_fill_pixels; // COUNT mode: pixels of the deferred-fill list
     uint32_t work[ASK_MAX_LEVELS];          // next work item a level kernel hands out
     uint32_t leaf_work;                     // next leaf the leaf kernel hands out
-    uint32_t fill_count;                    // entries in the deferred-fill list
-    uint32_t fill_work;                     // next fill row the fill kernel hands out
+    uint32_t fill_count;                    // bands in the deferred-fill list
+    uint32_t fill_work;                     // next band the leaf kernel's fill warps take
     uint32_t pad_;
 };
 

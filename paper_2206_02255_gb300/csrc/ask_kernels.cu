@@ -1,6 +1,7 @@
 // ask_kernels.cu -- exhaustive kernel and the Adaptive Serial Kernels (ASK)
-// pipeline: init, one level kernel per subdivision depth, deferred fills,
-// leaf kernel.
+// pipeline: init, one level kernel per subdivision depth, leaf kernel (which
+// also writes the deferred fills), and the fill kernel of the variants that
+// fill in a pass of their own.
 //
 // ASK (paper Sec. 5): the active regions of depth i sit in a device-resident
 // offset lookup table (read-OLT, Sec. 5.2).  One kernel per depth evaluates
@@ -26,8 +27,9 @@
 //  * decisions are compacted per warp: each lane keeps the outcome of one
 //    region, then one atomicAdd per list serves up to 32 regions (the
 //    block-scan + single atomic alternative of Sec. 5.3.1, at warp scope);
-//  * large uniform regions are filled by a separate HBM-bound fill kernel
-//    with 128-bit stores over all SMs; small ones in place by their warp;
+//  * small uniform regions are filled in place by their warp; large ones go
+//    to a fill list as bands of rows, written with 128-bit stores by the
+//    leaf kernel's fill warps beside its FP32 work (or by the fill kernel);
 //  * the OLTs are preallocated for the worst case, so nothing is resized
 //    between depths (Sec. 5.3.2 reallocates instead).
 #include <cuda_runtime.h>
