@@ -195,14 +195,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU reference (the oracle as it stands), all host cores
 # ---------------------------------------------------------------------------
-def cpu_reference_sample(C, g, r, B, seconds, seed=2206):
+def cpu_reference_sample(C, g, r, B, seconds, seed=2206, threads=None):
     """Render seeded initial regions with the CPU reference on every host
-    core until about ``seconds`` of wall time; returns (pixels, s, cores, regions)."""
+    core (or on ``threads`` of them) until about ``seconds`` of wall time;
+    returns (pixels, s, cores, regions)."""
     from concurrent.futures import ThreadPoolExecutor
     import oracle
     from paper_2206_02255_gb300 import inputs
     orc = oracle.default()
-    cores = oracle.default_threads()
+    cores = threads or oracle.default_threads()
     order = inputs.sample_initial_regions(g, g * g, seed)
     done_px = 0
     used = 0
@@ -502,9 +503,12 @@ def run_gpu(args):
     cpu = None
     if world == 1 and not args.no_cpu:
         px, t, cores, regions = cpu_reference_sample(C, g, r, B, 12.0)
+        px1, t1, _, regions1 = cpu_reference_sample(C, g, r, B, 4.0, threads=1)
         cpu = {"value": px / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d seeded initial regions of %dx%d (%d pixels) at n=%d, max_dwell=%d, "
-                         "g=%d r=%d B=%d" % (regions, g, g, px, n, M, g, r, B)}
+                         "g=%d r=%d B=%d" % (regions, g, g, px, n, M, g, r, B),
+               "single_thread": {"value": px1 / t1 / 1e9, "cores": 1,
+                                 "sample": "%d seeded initial regions (%d pixels)" % (regions1, px1)}}
 
     if rank == 0:
         line = {
