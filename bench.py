@@ -448,9 +448,9 @@ def run_gpu(args):
 
     # ---- the deferred-fill kernel against HBM write bandwidth --------------
     # algorithmic bytes: 4 per pixel of the regions it fills (large uniform
-    # regions; small ones are filled inside the level kernels)
-    # the fill kernel is timed alone (ASK_FLAG_SERIAL_FILL: on the render
-    # stream, every SM), since beside the leaf kernel it shares the SMs
+    # regions; small ones are filled inside the level kernels).  By default
+    # the leaf kernel's fill warps write these bands; ASK_FLAG_SERIAL_FILL
+    # runs the fill kernel alone over every SM, so its time can be read.
     roofline_fill = None
     for _ in range(5):
         one("ask", g, r, B, blk, ask.FLAG_TIMING | ask.FLAG_SERIAL_FILL)
