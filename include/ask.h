@@ -199,7 +199,7 @@ ask_status ask_render(ask_ctx *ctx, ask_method method, const ask_window *window,
 /* Same as ask_render but the map lands in host memory h_dwell (n*n uint32,
  * pageable or pinned; pinned is faster), and the call synchronises `stream`
  * before returning.  The context renders into its own device buffer.  For
- * ASK without stats (and without ASK_FLAG_STAGED_COPY) a map of 384 MiB or
+ * ASK without stats (and without ASK_FLAG_STAGED_COPY) a map of 192 MiB or
  * more is rendered in bands of initial-region rows -- independent
  * subtrees that cover contiguous map rows -- and each band is copied to the
  * host on a second stream while the next band renders; otherwise the whole

@@ -81,8 +81,11 @@ namespace ask {
 
 static uint32_t ceil_div(uint32_t a, uint32_t b) { return a / b + (a % b != 0u); }
 
-// Target bytes of map per band of the banded ask_render_host pipeline.
-constexpr uint64_t kBandBytes = 256ull << 20;
+// Target bytes of map per band of the banded ask_render_host pipeline.  At
+// n = 16384 (1 GiB) 8 bands of 128 MiB took 6.2 ms per call, 4 of 256 MiB
+// 6.45 ms, and 16 of 64 MiB 8.4 ms: a band's render must stay shorter than
+// its copy, and small bands leave the level kernels too few regions.
+constexpr uint64_t kBandBytes = 128ull << 20;
 
 bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px)
 {

@@ -307,7 +307,8 @@ def test_render_host_buffers(ctx, orc, asklib, method):
         assert first_diff(got.numpy().view(np.uint32), want) is None, (method, n, "staged")
 
 
-@pytest.mark.parametrize("n,g,r,B", [(12000, 8, 2, 32), (10500, 7, 3, 8), (16384, 64, 2, 16)])
+@pytest.mark.parametrize("n,g,r,B", [(12000, 8, 2, 32), (10500, 7, 3, 8), (16384, 64, 2, 16),
+                                     (7500, 5, 2, 16), (16384, 3, 4, 16)])
 def test_render_host_banded(ctx, orc, asklib, n, g, r, B):
     """Maps large enough for the banded host pipeline (several bands of
     initial-region rows, a ragged last band) equal the device-output render,
