@@ -12,7 +12,10 @@ The arithmetic lives in ``oracle.c`` (plain C, single precision, explicit
 * :func:`render_ms` -- serial recursive Mariani-Silver (Sec. 4.2.1, Sec. 6),
   with per-level statistics and an optional log of every region visited;
 * :func:`render_ms_region` -- one initial region of the g x g grid, for
-  sampled parity checks on maps too large to render on the CPU.
+  sampled parity checks on maps too large to render on the CPU;
+* :func:`dwell64`, :func:`pixel_to_c64`, :func:`render_exhaustive64`,
+  :func:`render_ms64` -- the same in double precision (deep zooms), the
+  window given in double.
 
 :class:`Oracle` wraps one build of the library; the module-level functions
 use the default build.  Tests also load deliberately broken builds through
@@ -34,6 +37,11 @@ MAX_LEVELS = 32
 class Window(ctypes.Structure):
     _fields_ = [("re_min", ctypes.c_float), ("re_max", ctypes.c_float),
                 ("im_min", ctypes.c_float), ("im_max", ctypes.c_float)]
+
+
+class Window64(ctypes.Structure):
+    _fields_ = [("re_min", ctypes.c_double), ("re_max", ctypes.c_double),
+                ("im_min", ctypes.c_double), ("im_max", ctypes.c_double)]
 
 
 class MSStats(ctypes.Structure):
@@ -73,6 +81,11 @@ def _win(window):
     return Window(re_min, re_max, im_min, im_max)
 
 
+def _win64(window):
+    re_min, re_max, im_min, im_max = window
+    return Window64(re_min, re_max, im_min, im_max)
+
+
 class Oracle:
     """One loaded build of the reference library."""
 
@@ -93,6 +106,18 @@ class Oracle:
                                        ctypes.c_void_p, u64, P(u64)]
         L.oracle_initial_region.restype = ctypes.c_int
         L.oracle_initial_region.argtypes = [u32, u32, u32, u32, P(u32), P(u32), P(u32), P(u32)]
+        f64 = ctypes.c_double
+        L.oracle_dwell64.restype = u32
+        L.oracle_dwell64.argtypes = [f64, f64, u32, u32]
+        L.oracle_pixel_to_c64.restype = None
+        L.oracle_pixel_to_c64.argtypes = [P(Window64), u32, u32, u32, P(f64), P(f64)]
+        L.oracle_render_exhaustive64.restype = ctypes.c_int
+        L.oracle_render_exhaustive64.argtypes = [P(Window64), u32, u32, u32, ctypes.c_void_p,
+                                                 ctypes.c_int, P(u64)]
+        L.oracle_render_ms64.restype = ctypes.c_int
+        L.oracle_render_ms64.argtypes = [P(Window64), u32, u32, u32, u32, u32, u32,
+                                         ctypes.c_void_p, ctypes.c_int, P(MSStats),
+                                         ctypes.c_void_p, u64, P(u64)]
         L.oracle_render_ms_region.restype = ctypes.c_int
         L.oracle_render_ms_region.argtypes = [P(Window), u32, u32, u32, u32, u32, u32,
                                               u32, u32, ctypes.c_void_p, ctypes.c_size_t,
@@ -112,40 +137,54 @@ class Oracle:
                                    ctypes.byref(ci))
         return cr.value, ci.value
 
+    def dwell64(self, cr, ci, max_dwell, flags=0):
+        """Dwell of the point c = cr + i*ci in double precision."""
+        return int(self.lib.oracle_dwell64(cr, ci, max_dwell, flags))
+
+    def pixel_to_c64(self, window, n, px, py):
+        """The double-precision point sampled by pixel (px, py)."""
+        cr, ci = ctypes.c_double(), ctypes.c_double()
+        w = _win64(window)
+        self.lib.oracle_pixel_to_c64(ctypes.byref(w), n, px, py, ctypes.byref(cr),
+                                     ctypes.byref(ci))
+        return cr.value, ci.value
+
     def render_exhaustive(self, window, n, max_dwell, flags=0, threads=None,
-                          return_iterations=False):
-        """n x n uint32 map, out[py, px] = dwell at pixel (px, py)."""
+                          return_iterations=False, fp64=False):
+        """n x n uint32 map, out[py, px] = dwell at pixel (px, py).  With
+        fp64 the window and the arithmetic are double precision."""
         out = np.empty((n, n), dtype=np.uint32)
         it = ctypes.c_uint64()
-        w = _win(window)
-        rc = self.lib.oracle_render_exhaustive(ctypes.byref(w), n, max_dwell, flags,
-                                               out.ctypes.data, threads or default_threads(),
-                                               ctypes.byref(it))
+        w = _win64(window) if fp64 else _win(window)
+        fn = self.lib.oracle_render_exhaustive64 if fp64 else self.lib.oracle_render_exhaustive
+        rc = fn(ctypes.byref(w), n, max_dwell, flags, out.ctypes.data,
+                threads or default_threads(), ctypes.byref(it))
         if rc != 0:
             raise ValueError("oracle_render_exhaustive: invalid arguments (rc=%d)" % rc)
         return (out, int(it.value)) if return_iterations else out
 
-    def render_ms(self, window, n, max_dwell, g, r, B, flags=0, threads=None, log=False):
-        """Mariani-Silver map.  Returns (map, stats dict[, region log array])."""
+    def render_ms(self, window, n, max_dwell, g, r, B, flags=0, threads=None, log=False,
+                  fp64=False):
+        """Mariani-Silver map.  Returns (map, stats dict[, region log array]).
+        With fp64 the window and the arithmetic are double precision."""
         out = np.empty((n, n), dtype=np.uint32)
         st = MSStats()
-        w = _win(window)
+        w = _win64(window) if fp64 else _win(window)
+        fn = self.lib.oracle_render_ms64 if fp64 else self.lib.oracle_render_ms
         if log:
             cap = 1 << 16
             while True:
                 buf = np.zeros(cap, dtype=REGION_DTYPE)
                 ln = ctypes.c_uint64()
-                rc = self.lib.oracle_render_ms(ctypes.byref(w), n, max_dwell, g, r, B, flags,
-                                               out.ctypes.data, 1, ctypes.byref(st),
-                                               buf.ctypes.data, cap, ctypes.byref(ln))
+                rc = fn(ctypes.byref(w), n, max_dwell, g, r, B, flags, out.ctypes.data, 1,
+                        ctypes.byref(st), buf.ctypes.data, cap, ctypes.byref(ln))
                 if rc != 0:
                     raise ValueError("oracle_render_ms: invalid arguments (rc=%d)" % rc)
                 if ln.value <= cap:
                     return out, st.as_dict(), buf[:ln.value].copy()
                 cap = int(ln.value)
-        rc = self.lib.oracle_render_ms(ctypes.byref(w), n, max_dwell, g, r, B, flags,
-                                       out.ctypes.data, threads or default_threads(),
-                                       ctypes.byref(st), None, 0, None)
+        rc = fn(ctypes.byref(w), n, max_dwell, g, r, B, flags, out.ctypes.data,
+                threads or default_threads(), ctypes.byref(st), None, 0, None)
         if rc != 0:
             raise ValueError("oracle_render_ms: invalid arguments (rc=%d)" % rc)
         return out, st.as_dict()
@@ -210,3 +249,19 @@ def initial_region(*a, **k):
 
 def render_ms_region(*a, **k):
     return default().render_ms_region(*a, **k)
+
+
+def dwell64(*a, **k):
+    return default().dwell64(*a, **k)
+
+
+def pixel_to_c64(*a, **k):
+    return default().pixel_to_c64(*a, **k)
+
+
+def render_exhaustive64(window, n, max_dwell, **k):
+    return default().render_exhaustive(window, n, max_dwell, fp64=True, **k)
+
+
+def render_ms64(window, n, max_dwell, g, r, B, **k):
+    return default().render_ms(window, n, max_dwell, g, r, B, fp64=True, **k)

@@ -76,6 +76,28 @@ uint32_t oracle_dwell(float cr, float ci, uint32_t max_dwell, uint32_t flags)
     return d;
 }
 
+/* The same iteration in double precision (deep zooms, where neighbouring
+ * pixels are closer than single precision can tell apart). */
+uint32_t oracle_dwell64(double cr, double ci, uint32_t max_dwell, uint32_t flags)
+{
+    double zr = 0.0, zi = 0.0;
+    uint32_t d = 0;
+    while (d < max_dwell) {
+        double zi2 = zi * zi;
+        double m = fma(zr, zr, zi2);
+        int bounded = (flags & ORACLE_ESCAPE_LE) ? (m <= 4.0) : (m < 4.0);
+        if (!bounded)
+            break;
+        double t = fma(-zi, zi, cr);
+        double nzr = fma(zr, zr, t);
+        double nzi = fma(zr + zr, zi, ci);
+        zr = nzr;
+        zi = nzi;
+        d++;
+    }
+    return d;
+}
+
 /* Pixel -> point of the complex plane (corner sampling, see header). */
 void oracle_pixel_to_c(const oracle_window *win, uint32_t n, uint32_t px,
                        uint32_t py, float *cr, float *ci)
@@ -86,26 +108,57 @@ void oracle_pixel_to_c(const oracle_window *win, uint32_t n, uint32_t px,
     *ci = fmaf((float)py, dy, win->im_min);
 }
 
-static uint32_t pixel_dwell(const oracle_window *win, uint32_t n,
+void oracle_pixel_to_c64(const oracle_window64 *win, uint32_t n, uint32_t px,
+                         uint32_t py, double *cr, double *ci)
+{
+    double dx = (win->re_max - win->re_min) / (double)n;
+    double dy = (win->im_max - win->im_min) / (double)n;
+    *cr = fma((double)px, dx, win->re_min);
+    *ci = fma((double)py, dy, win->im_min);
+}
+
+/* The window of a map in either precision: exactly one pointer is set. */
+typedef struct {
+    const oracle_window *w32;
+    const oracle_window64 *w64;
+} any_window;
+
+static uint32_t pixel_dwell(const any_window *win, uint32_t n,
                             uint32_t max_dwell, uint32_t flags, uint32_t px,
                             uint32_t py)
 {
+    if (win->w64) {
+        double cr, ci;
+        oracle_pixel_to_c64(win->w64, n, px, py, &cr, &ci);
+        return oracle_dwell64(cr, ci, max_dwell, flags);
+    }
     float cr, ci;
-    oracle_pixel_to_c(win, n, px, py, &cr, &ci);
+    oracle_pixel_to_c(win->w32, n, px, py, &cr, &ci);
     return oracle_dwell(cr, ci, max_dwell, flags);
 }
 
 static int window_ok(const oracle_window *w)
 {
-    return isfinite(w->re_min) && isfinite(w->re_max) && isfinite(w->im_min) &&
+    return w && isfinite(w->re_min) && isfinite(w->re_max) && isfinite(w->im_min) &&
            isfinite(w->im_max) && w->re_max > w->re_min && w->im_max > w->im_min;
+}
+
+static int window64_ok(const oracle_window64 *w)
+{
+    return w && isfinite(w->re_min) && isfinite(w->re_max) && isfinite(w->im_min) &&
+           isfinite(w->im_max) && w->re_max > w->re_min && w->im_max > w->im_min;
+}
+
+static int any_window_ok(const any_window *w)
+{
+    return w->w64 ? window64_ok(w->w64) : window_ok(w->w32);
 }
 
 /* ------------------------------------------------------------------ */
 /* Exhaustive map (Sec. 4.1, Eq. 1-2): one dwell per pixel.             */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    const oracle_window *win;
+    const any_window *win;
     uint32_t n, max_dwell, flags;
     uint32_t row_begin, row_end;
     uint32_t *out;
@@ -126,11 +179,11 @@ static void *ex_rows(void *arg)
     return NULL;
 }
 
-int oracle_render_exhaustive(const oracle_window *win, uint32_t n,
+static int render_exhaustive(const any_window *win, uint32_t n,
                              uint32_t max_dwell, uint32_t flags, uint32_t *out,
                              int nthreads, uint64_t *iterations)
 {
-    if (!win || !out || n == 0 || max_dwell == 0 || !window_ok(win))
+    if (!out || n == 0 || max_dwell == 0 || !any_window_ok(win))
         return -1;
     if (nthreads < 1)
         nthreads = 1;
@@ -167,12 +220,28 @@ int oracle_render_exhaustive(const oracle_window *win, uint32_t n,
     return 0;
 }
 
+int oracle_render_exhaustive(const oracle_window *win, uint32_t n,
+                             uint32_t max_dwell, uint32_t flags, uint32_t *out,
+                             int nthreads, uint64_t *iterations)
+{
+    any_window w = {win, NULL};
+    return render_exhaustive(&w, n, max_dwell, flags, out, nthreads, iterations);
+}
+
+int oracle_render_exhaustive64(const oracle_window64 *win, uint32_t n,
+                               uint32_t max_dwell, uint32_t flags, uint32_t *out,
+                               int nthreads, uint64_t *iterations)
+{
+    any_window w = {NULL, win};
+    return render_exhaustive(&w, n, max_dwell, flags, out, nthreads, iterations);
+}
+
 /* ------------------------------------------------------------------ */
 /* Mariani-Silver subdivision (Sec. 4.2.1 and Sec. 6), serial and       */
 /* depth first.                                                         */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    const oracle_window *win;
+    const any_window *win;
     uint32_t n, max_dwell, g, r, B, flags;
     /* output: the full map (out_stride == n, origin 0,0) or one initial
      * region's tile (origin ox,oy, row stride out_stride) */
@@ -303,10 +372,10 @@ static int initial_region(uint32_t n, uint32_t g, uint32_t gx, uint32_t gy,
     return 1;
 }
 
-static int ms_args_ok(const oracle_window *win, uint32_t n, uint32_t max_dwell,
+static int ms_args_ok(const any_window *win, uint32_t n, uint32_t max_dwell,
                       uint32_t g, uint32_t r, uint32_t B)
 {
-    return win && window_ok(win) && n > 0 && max_dwell > 0 && g > 0 && r >= 2 && B > 0;
+    return any_window_ok(win) && n > 0 && max_dwell > 0 && g > 0 && r >= 2 && B > 0;
 }
 
 typedef struct {
@@ -342,7 +411,7 @@ static void add_stats(oracle_ms_stats *a, const oracle_ms_stats *b)
     a->iterations += b->iterations;
 }
 
-int oracle_render_ms(const oracle_window *win, uint32_t n, uint32_t max_dwell,
+static int render_ms(const any_window *win, uint32_t n, uint32_t max_dwell,
                      uint32_t g, uint32_t r, uint32_t B, uint32_t flags,
                      uint32_t *out, int nthreads, oracle_ms_stats *stats,
                      oracle_region *log, uint64_t log_cap, uint64_t *log_len)
@@ -403,6 +472,26 @@ int oracle_render_ms(const oracle_window *win, uint32_t n, uint32_t max_dwell,
     return 0;
 }
 
+int oracle_render_ms(const oracle_window *win, uint32_t n, uint32_t max_dwell,
+                     uint32_t g, uint32_t r, uint32_t B, uint32_t flags,
+                     uint32_t *out, int nthreads, oracle_ms_stats *stats,
+                     oracle_region *log, uint64_t log_cap, uint64_t *log_len)
+{
+    any_window w = {win, NULL};
+    return render_ms(&w, n, max_dwell, g, r, B, flags, out, nthreads, stats, log, log_cap,
+                     log_len);
+}
+
+int oracle_render_ms64(const oracle_window64 *win, uint32_t n, uint32_t max_dwell,
+                       uint32_t g, uint32_t r, uint32_t B, uint32_t flags,
+                       uint32_t *out, int nthreads, oracle_ms_stats *stats,
+                       oracle_region *log, uint64_t log_cap, uint64_t *log_len)
+{
+    any_window w = {NULL, win};
+    return render_ms(&w, n, max_dwell, g, r, B, flags, out, nthreads, stats, log, log_cap,
+                     log_len);
+}
+
 int oracle_initial_region(uint32_t n, uint32_t g, uint32_t gx, uint32_t gy,
                           uint32_t *x0, uint32_t *y0, uint32_t *w, uint32_t *h)
 {
@@ -418,11 +507,12 @@ int oracle_render_ms_region(const oracle_window *win, uint32_t n,
                             uint32_t gy, uint32_t *tile, size_t tile_stride,
                             oracle_ms_stats *stats)
 {
-    if (!tile || !ms_args_ok(win, n, max_dwell, g, r, B) || gx >= g || gy >= g)
+    any_window aw = {win, NULL};
+    if (!tile || !ms_args_ok(&aw, n, max_dwell, g, r, B) || gx >= g || gy >= g)
         return -1;
     ms_job j;
     memset(&j, 0, sizeof(j));
-    j.win = win;
+    j.win = &aw;
     j.n = n;
     j.max_dwell = max_dwell;
     j.g = g;

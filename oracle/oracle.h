@@ -28,6 +28,11 @@ typedef struct {
     float re_min, re_max, im_min, im_max;
 } oracle_window;
 
+/* Double-precision window, for the FP64 (deep-zoom) maps. */
+typedef struct {
+    double re_min, re_max, im_min, im_max;
+} oracle_window64;
+
 typedef struct {
     uint32_t levels;
     uint32_t pad_;
@@ -57,6 +62,22 @@ int oracle_render_ms(const oracle_window *win, uint32_t n, uint32_t max_dwell,
                      oracle_region *log, uint64_t log_cap, uint64_t *log_len);
 int oracle_initial_region(uint32_t n, uint32_t g, uint32_t gx, uint32_t gy,
                           uint32_t *x0, uint32_t *y0, uint32_t *w, uint32_t *h);
+/* The same dwell, pixel mapping and maps in double precision, with the same
+ * operation sequence (each operation rounded once to double):
+ *   zi2 = zi*zi; m = fma(zr, zr, zi2); t = fma(-zi, zi, cr);
+ *   zr' = fma(zr, zr, t); zi' = fma(zr + zr, zi, ci);
+ *   dx = (re_max - re_min) / n; cr = fma(px, dx, re_min) (likewise ci). */
+uint32_t oracle_dwell64(double cr, double ci, uint32_t max_dwell, uint32_t flags);
+void oracle_pixel_to_c64(const oracle_window64 *win, uint32_t n, uint32_t px,
+                         uint32_t py, double *cr, double *ci);
+int oracle_render_exhaustive64(const oracle_window64 *win, uint32_t n,
+                               uint32_t max_dwell, uint32_t flags, uint32_t *out,
+                               int nthreads, uint64_t *iterations);
+int oracle_render_ms64(const oracle_window64 *win, uint32_t n, uint32_t max_dwell,
+                       uint32_t g, uint32_t r, uint32_t B, uint32_t flags,
+                       uint32_t *out, int nthreads, oracle_ms_stats *stats,
+                       oracle_region *log, uint64_t log_cap, uint64_t *log_len);
+
 int oracle_render_ms_region(const oracle_window *win, uint32_t n,
                             uint32_t max_dwell, uint32_t g, uint32_t r,
                             uint32_t B, uint32_t flags, uint32_t gx,

@@ -267,6 +267,40 @@ def test_ask_repeat_and_async(ctx, orc, asklib):
         assert np.array_equal(o.cpu().numpy().view(np.uint32), want)
 
 
+def test_contexts_on_concurrent_streams(orc, asklib):
+    """Three contexts render different maps on three streams at once (their
+    kernels share the GPU; each context owns its tables and counters): every
+    map equals the reference, and a render with stats on one stream reports
+    that context's own counts."""
+    import torch
+    specs = [(inputs.WINDOW_PAPER, 2048, 1024, 16, 4, 16), (inputs.WINDOW_WIDE, 1500, 600, 8, 2, 8),
+             ((-0.8, -0.6, 0.05, 0.30), 1111, 2000, 5, 3, 16)]
+    ctxs = [asklib.Context(0) for _ in specs]
+    streams = [torch.cuda.Stream() for _ in specs]
+    try:
+        outs = []
+        for c, s, (win, n, M, g, r, B) in zip(ctxs, streams, specs):
+            with torch.cuda.stream(s):
+                outs.append([c.render("ask", win, n, M, params(asklib, g, r, B), stream=s)
+                             for _ in range(2)])
+        for c, s in zip(ctxs, streams):
+            s.synchronize()
+            c.check(s)
+        for (win, n, M, g, r, B), o2 in zip(specs, outs):
+            want, ost = orc.render_ms(win, n, M, g, r, B)
+            for o in o2:
+                assert first_diff(o.cpu().numpy().view(np.uint32), want) is None, (n, g)
+        win, n, M, g, r, B = specs[1]
+        _, ost = orc.render_ms(win, n, M, g, r, B)
+        with torch.cuda.stream(streams[1]):
+            _, st = ctxs[1].render("ask", win, n, M, params(asklib, g, r, B), stream=streams[1],
+                                   stats=True)
+        assert st["regions_per_level"][:ost["levels"]] == ost["regions_per_level"]
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 def test_render_host(ctx, orc, asklib):
     C = inputs.C0
     win, n, M = C["window"], C["n"], C["max_dwell"]
