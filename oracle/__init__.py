@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, the package's ``smoke()`` check
 and the benchmark's CPU-baseline leg import this module.  The GPU library and
 its Python binding never import it, and it imports nothing from them.
 
-The arithmetic lives in ``oracle.c`` (plain C, single precision, explicit
-``fmaf``); this module only marshals numpy buffers.  Functions:
+The arithmetic lives in ``oracle.c`` (plain C, single precision with
+explicit ``fmaf``, and the same sequence in double with ``fma`` for deep
+zooms); this module only marshals numpy buffers.  Functions:
 
 * :func:`dwell` -- dwell of one point (Sec. 6 of the paper);
 * :func:`render_exhaustive` -- the per-pixel map (Sec. 4.1, Eq. 1-2);

@@ -1,10 +1,12 @@
-"""Exact single-precision arithmetic on rationals, in pure Python.
+"""Exact single- and double-precision arithmetic on rationals, in pure Python.
 
 Used only by the tests, to brute-force tiny dwell maps without any C
 compiler, libm or hardware FMA in the loop: every operation is carried out
 exactly on ``fractions.Fraction`` values and then rounded once to the
 nearest float32 (ties to even), which is what IEEE 754 prescribes for a
-single-precision add, multiply and fused multiply-add.
+single-precision add, multiply and fused multiply-add.  The ``*64``
+functions do the same with rounding to the nearest binary64 value (53-bit
+significand), for the double-precision maps of deep zooms.
 """
 from fractions import Fraction
 import struct
@@ -12,8 +14,10 @@ import struct
 _HALF = Fraction(1, 2)
 
 
-def rn32(q):
-    """Round the rational ``q`` to the nearest float32 (ties to even)."""
+def _round(q, bits, emin, emax):
+    """Round the rational ``q`` to the nearest binary floating-point value
+    with a ``bits``-bit significand, smallest normal exponent ``emin`` and
+    overflow threshold 2**emax (ties to even)."""
     q = Fraction(q)
     if q == 0:
         return Fraction(0)
@@ -25,16 +29,26 @@ def rn32(q):
         e -= 1
     while Fraction(2) ** (e + 1) <= a:
         e += 1
-    quantum_exp = max(e - 23, -149)          # 24-bit significand; subnormals below 2**-126
+    quantum_exp = max(e - (bits - 1), emin - (bits - 1))   # subnormals below 2**emin
     scaled = a / Fraction(2) ** quantum_exp
     fl = scaled.numerator // scaled.denominator
     rem = scaled - fl
     if rem > _HALF or (rem == _HALF and fl % 2 == 1):
         fl += 1
     res = fl * Fraction(2) ** quantum_exp
-    if res >= Fraction(2) ** 128:
-        raise OverflowError("float32 overflow in a brute-force case")
+    if res >= Fraction(2) ** emax:
+        raise OverflowError("overflow in a brute-force case")
     return sign * res
+
+
+def rn32(q):
+    """Round the rational ``q`` to the nearest float32 (ties to even)."""
+    return _round(q, 24, -126, 128)
+
+
+def rn64(q):
+    """Round the rational ``q`` to the nearest binary64 double (ties to even)."""
+    return _round(q, 53, -1022, 1024)
 
 
 def f32(x):
@@ -81,4 +95,47 @@ def exhaustive(window, n, max_dwell):
         for px in range(n):
             cr, ci = pixel_c(window, n, px, py)
             out[py][px] = dwell(cr, ci, max_dwell)
+    return out
+
+
+# --------------------------------------------------------------------------
+# double precision: the same definitions with every operation rounded once
+# to binary64
+# --------------------------------------------------------------------------
+def f64(x):
+    """The double nearest to a Python number, as a Fraction."""
+    return rn64(Fraction(x))
+
+
+def dwell64(cr, ci, max_dwell, le=False):
+    """Dwell with each operation rounded once to double."""
+    cr, ci = f64(cr), f64(ci)
+    zr = zi = Fraction(0)
+    d = 0
+    while d < max_dwell:
+        zi2 = rn64(zi * zi)
+        m = rn64(zr * zr + zi2)
+        if not (m <= 4 if le else m < 4):
+            break
+        t = rn64(-zi * zi + cr)
+        nzr = rn64(zr * zr + t)
+        nzi = rn64(rn64(zr + zr) * zi + ci)
+        zr, zi = nzr, nzi
+        d += 1
+    return d
+
+
+def pixel_c64(window, n, px, py):
+    re_min, re_max, im_min, im_max = (f64(v) for v in window)
+    dx = rn64(rn64(re_max - re_min) / n)
+    dy = rn64(rn64(im_max - im_min) / n)
+    return rn64(px * dx + re_min), rn64(py * dy + im_min)
+
+
+def exhaustive64(window, n, max_dwell):
+    out = [[0] * n for _ in range(n)]
+    for py in range(n):
+        for px in range(n):
+            cr, ci = pixel_c64(window, n, px, py)
+            out[py][px] = dwell64(cr, ci, max_dwell)
     return out

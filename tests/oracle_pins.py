@@ -268,7 +268,100 @@ def pin_threads_and_regions(orc):
     assert it == sa["iterations"]
 
 
+# --------------------------------------------------------------------------
+# double precision (deep zooms)
+# --------------------------------------------------------------------------
+# A window 2^-28 wide in the upper spiral arm: zoom ~ 7e9 over the paper's
+# 2 x 2 window, far past what single precision resolves (the float32 window
+# collapses to one column of c), with dwells of 67 to 132.
+DEEP_WINDOW = (-0.10109636384562, -0.10109636384562 + 2.0 ** -28,
+               0.95628651080914, 0.95628651080914 + 2.0 ** -28)
+# Seahorse valley, 2^-30 wide: dwells 1021 to 2000 at a cap of 2000.
+SEAHORSE_WINDOW = (-0.743643887037151, -0.743643887037151 + 2.0 ** -30,
+                   0.13182590420533, 0.13182590420533 + 2.0 ** -30)
+
+
+def pin_closed_forms64(orc):
+    """Every hand-computed orbit of the fixture takes values with few
+    significant bits (exact in float32, hence in double too), so the
+    double-precision dwell must give the same counts under both readings."""
+    for cr, ci, M, flags, d in closed_forms():
+        assert orc.dwell64(cr, ci, M, flags) == d, (cr, ci, M, flags, d)
+
+
+def pin_exact_points64(orc):
+    """Random double points, and points 1e-12 apart that float32 cannot tell
+    apart, against the exact-rational brute force rounded to binary64."""
+    rng = random.Random(20220606)
+    for _ in range(100):
+        cr, ci = rng.uniform(-2.2, 1.0), rng.uniform(-1.4, 1.4)
+        assert orc.dwell64(cr, ci, 48) == f32exact.dwell64(cr, ci, 48), (cr, ci)
+    re0, im0 = DEEP_WINDOW[0], DEEP_WINDOW[2]
+    seen = set()
+    for k in range(12):
+        cr, ci = re0 + k * 1e-12, im0 + (k % 5) * 3e-12
+        d = orc.dwell64(cr, ci, 400)
+        assert d == f32exact.dwell64(cr, ci, 400), (cr, ci)
+        seen.add(d)
+    assert len(seen) > 1   # the points are distinct in double
+
+
+def pin_exact_tiny_maps64(orc):
+    """Tiny double-precision maps, pixel for pixel, against the brute force
+    (asymmetric windows; one of them a deep zoom), and the pixel -> c map."""
+    cases = [((-2.0, 0.5, -1.1, 1.3), 3, 40), ((-0.8, -0.6, 0.05, 0.30), 5, 60),
+             (DEEP_WINDOW, 7, 200)]
+    for win, n, M in cases:
+        got = orc.render_exhaustive(win, n, M, threads=2, fp64=True)
+        want = np.array(f32exact.exhaustive64(win, n, M), dtype=np.uint32)
+        assert np.array_equal(got, want), (win, n, M)
+    rng = random.Random(8)
+    for _ in range(60):
+        a, b = sorted(rng.uniform(-2.5, 2.5) for _ in range(2))
+        c, d = sorted(rng.uniform(-2.5, 2.5) for _ in range(2))
+        if b - a < 1e-9 or d - c < 1e-9:
+            continue
+        n = rng.randint(1, 70000)
+        px, py = rng.randrange(n), rng.randrange(n)
+        want = tuple(float(v) for v in f32exact.pixel_c64((a, b, c, d), n, px, py))
+        assert orc.pixel_to_c64((a, b, c, d), n, px, py) == want, ((a, b, c, d), n, px, py)
+
+
+def pin_deep_zoom64(orc):
+    """Where the spacing is a power of two the double mapping is exact:
+    2^-30 / 64 = 2^-36 and every c = re_min + px 2^-36 is a double.  Sampled
+    pixels of the seahorse-valley map (dwells near 1000 to 2000) against the
+    brute force; Mariani-Silver with fills off equals the exhaustive map."""
+    win, n, M = SEAHORSE_WINDOW, 64, 2000
+    for px, py in [(0, 0), (63, 0), (17, 40), (63, 63)]:
+        assert orc.pixel_to_c64(win, n, px, py) == (win[0] + px * 2.0 ** -36,
+                                                    win[2] + py * 2.0 ** -36)
+    m = orc.render_exhaustive(win, n, M, threads=4, fp64=True)
+    assert m.min() > 1000 and len(np.unique(m)) > 300
+    rng = random.Random(64)
+    for _ in range(4):
+        px, py = rng.randrange(n), rng.randrange(n)
+        cr, ci = orc.pixel_to_c64(win, n, px, py)
+        assert m[py, px] == f32exact.dwell64(cr, ci, M), (px, py)
+    ms, _ = orc.render_ms(win, n, M, 4, 2, 4, flags=NO_FILL, threads=2, fp64=True)
+    assert np.array_equal(ms, m)
+
+
+def pin_ms64_invariants(orc):
+    """The recursion's invariants (tiling, uniform perimeters of filled
+    regions, children and stopping side) on double-precision maps."""
+    for win, n, M, g, r, B in [(DEEP_WINDOW, 64, 300, 4, 2, 4), (DEEP_WINDOW, 100, 300, 3, 2, 5),
+                               (SEAHORSE_WINDOW, 96, 2000, 2, 3, 4),
+                               ((-1.25066, -1.25066 + 2.0 ** -20, 0.02012, 0.02012 + 2.0 ** -20),
+                                128, 1200, 4, 4, 4)]:
+        ex = orc.render_exhaustive(win, n, M, threads=2, fp64=True)
+        ms, st, log = orc.render_ms(win, n, M, g, r, B, log=True, fp64=True)
+        check_region_log(ex, ms, st, log, n, g, r, B)
+        assert st["fills_per_level"] != [0] * len(st["fills_per_level"]), (n, g)
+
+
 ALL_PINS = [pin_closed_forms, pin_exact_points, pin_exact_tiny_maps,
             pin_c0_pixels, pin_symmetry_and_area, pin_no_fill_equals_exhaustive,
             pin_tree_by_hand, pin_ms_invariants, pin_uniform_windows, pin_stopping_side,
-            pin_threads_and_regions]
+            pin_threads_and_regions, pin_closed_forms64, pin_exact_points64,
+            pin_exact_tiny_maps64, pin_deep_zoom64, pin_ms64_invariants]

@@ -35,6 +35,19 @@ MUTANTS = [
     ("border_misses_right_column", "uint32_t step = edge_row ? 1u : (w > 1 ? w - 1 : 1u);",
      "uint32_t step = edge_row ? 1u : w;"),
     ("floor_initial_side", "uint32_t s0 = ceil_div(n, g);", "uint32_t s0 = n / g ? n / g : 1;"),
+    # the double-precision (deep-zoom) functions
+    ("dropped_factor_two_64", "double nzi = fma(zr + zr, zi, ci);", "double nzi = fma(zr, zi, ci);"),
+    ("wrong_sign_re_64", "double t = fma(-zi, zi, cr);", "double t = fma(zi, zi, cr);"),
+    ("escape_le_64", ": (m < 4.0);", ": (m <= 4.0);"),
+    ("state_in_float_64", "double zr = 0.0, zi = 0.0;", "float zr = 0.0f, zi = 0.0f;"),
+    ("transposed_operand_64", "*ci = fma((double)py, dy, win->im_min);",
+     "*ci = fma((double)py, dx, win->im_min);"),
+    ("c_rounded_to_float_64", "*cr = fma((double)px, dx, win->re_min);",
+     "*cr = (float)fma((double)px, dx, win->re_min);"),
+    ("center_sampling_64", "*ci = fma((double)py, dy, win->im_min);",
+     "*ci = fma((double)py + 0.5, dy, win->im_min);"),
+    ("map_in_float_64", "return oracle_dwell64(cr, ci, max_dwell, flags);",
+     "return oracle_dwell((float)cr, (float)ci, max_dwell, flags);"),
 ]
 
 
