@@ -29,6 +29,9 @@
  *       zi2 = zi*zi; m = fmaf(zr, zr, zi2);            -- |z|^2
  *       t = fmaf(-zi, zi, cr); zr' = fmaf(zr, zr, t);   -- zr^2 - zi^2 + cr
  *       zi' = fmaf(zr + zr, zi, ci);                    -- 2 zr zi + ci
+ *     and, for deep zooms where single precision cannot separate
+ *     neighbouring pixels, the same sequence with every operation rounded
+ *     once to double (the *64 functions, window given in double);
  *   - pixel (px, py) samples c at its corner:
  *       dx = (re_max - re_min) / n, dy = (im_max - im_min) / n  (float)
  *       cr = fmaf(px, dx, re_min), ci = fmaf(py, dy, im_min)
