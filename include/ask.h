@@ -26,6 +26,9 @@
  * samples c = (fma(px, dx, re_min), fma(py, dy, im_min)) with
  * dx = (re_max - re_min) / n and dy = (im_max - im_min) / n in float.
  *
+ * ask_render64 renders the exhaustive and ASK maps with the same sequence in
+ * double precision, for deep zooms.
+ *
  * Output layout: uint32 dwell[py * n + px], row-major, py = 0 <-> im_min.
  *
  * Subdivision (ASK and CDP2): initial regions of side s0 = ceil(n / g);
@@ -274,6 +277,30 @@ ask_status ask_plan_levels(uint32_t n, uint32_t g, uint32_t r, uint32_t B,
  * stream.  Each call clears the counters it needs on its stream first. */
 ask_status ask_render_noalloc(const ask_window *window, uint32_t n, uint32_t max_dwell,
                               const ask_params *params, uint32_t *d_dwell, void *stream);
+
+/* Window of a double-precision render. */
+typedef struct {
+    double re_min, re_max, im_min, im_max;
+} ask_window64;
+
+/* Render in double precision, for deep zooms: past a zoom of about 1e4 over
+ * the paper's 2 x 2 window (Sec. 6.1) the pixels of a large map are closer
+ * together than single precision separates, and neighbouring columns would
+ * share one c.  The same arithmetic sequence as the single-precision methods
+ * with every operation rounded once to binary64 (zi2 = zi*zi,
+ * m = fma(zr, zr, zi2), while m < 4: zr' = fma(zr, zr, fma(-zi, zi, cr)),
+ * zi' = fma(zr + zr, zi, ci)); pixel (px, py) samples
+ * c = (fma(px, dx, re_min), fma(py, dy, im_min)) with
+ * dx = (re_max - re_min) / n and dy = (im_max - im_min) / n in double.
+ * Methods ASK_METHOD_EXHAUSTIVE and ASK_METHOD_ASK (same subdivision rule,
+ * Sec. 4.2.1 and Sec. 5; one warp per region, so g should give a few
+ * thousand initial regions); ASK_METHOD_CDP2 returns ASK_EINVAL.
+ * params->flags: 0 or ASK_FLAG_COUNT.  Output, ownership, stream, stats and
+ * error behaviour as ask_render (ms_fill is 0: uniform regions are filled
+ * by the level kernels). */
+ask_status ask_render64(ask_ctx *ctx, ask_method method, const ask_window64 *window,
+                        uint32_t n, uint32_t max_dwell, const ask_params *params,
+                        uint32_t *d_dwell, void *stream, ask_stats *stats);
 
 /* Human-readable name of a status code (static storage). */
 const char *ask_status_str(ask_status status);

@@ -38,6 +38,11 @@ class Window(ctypes.Structure):
                 ("im_min", ctypes.c_float), ("im_max", ctypes.c_float)]
 
 
+class Window64(ctypes.Structure):
+    _fields_ = [("re_min", ctypes.c_double), ("re_max", ctypes.c_double),
+                ("im_min", ctypes.c_double), ("im_max", ctypes.c_double)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("g", ctypes.c_uint32), ("r", ctypes.c_uint32), ("B", ctypes.c_uint32),
                 ("block_x", ctypes.c_uint32), ("block_y", ctypes.c_uint32),
@@ -114,6 +119,9 @@ SIGNATURES = {
     "ask_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _P(Window), ctypes.c_uint32,
                                   ctypes.c_uint32, _P(Params), ctypes.c_void_p, ctypes.c_void_p,
                                   _P(Stats)]),
+    "ask_render64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _P(Window64), ctypes.c_uint32,
+                                    ctypes.c_uint32, _P(Params), ctypes.c_void_p, ctypes.c_void_p,
+                                    _P(Stats)]),
     "ask_render_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _P(Window), ctypes.c_uint32,
                                        ctypes.c_uint32, _P(Params), ctypes.c_void_p,
                                        ctypes.c_void_p, _P(Stats)]),
@@ -237,6 +245,10 @@ def _window(w):
     return w if isinstance(w, Window) else Window(*[float(v) for v in w])
 
 
+def _window64(w):
+    return w if isinstance(w, Window64) else Window64(*[float(v) for v in w])
+
+
 class Context:
     """An ``ask_ctx`` on one CUDA device; owns the library's scratch memory."""
 
@@ -299,6 +311,27 @@ class Context:
                               ctypes.byref(st_obj) if st_obj is not None else None)
         if st != OK:
             self._raise(st, "ask_render")
+        return (out, st_obj.as_dict()) if stats else out
+
+    def render64(self, method, window, n, max_dwell, params=None, out=None, stream=None,
+                 stats=False):
+        """Double-precision render (deep zooms) of ``window`` given in double:
+        "exhaustive" or "ask"; otherwise as :meth:`render`."""
+        import torch
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.int32, device="cuda:%d" % self.device)
+        if not out.is_cuda or out.numel() != n * n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA tensor of n*n elements")
+        if out.element_size() != 4:
+            raise ValueError("out must have 4-byte elements")
+        s = stream if stream is not None else torch.cuda.current_stream(out.device)
+        st_obj = Stats() if stats else None
+        st = lib().ask_render64(self._h, _method(method), ctypes.byref(_window64(window)), n,
+                                max_dwell, ctypes.byref(params) if params is not None else None,
+                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream),
+                                ctypes.byref(st_obj) if st_obj is not None else None)
+        if st != OK:
+            self._raise(st, "ask_render64")
         return (out, st_obj.as_dict()) if stats else out
 
     def render_host(self, method, window, n, max_dwell, params=None, out=None, stream=None,

@@ -3,8 +3,10 @@
 Every CUDA translation unit is compiled for sm_103a only, in parallel:
 
 * ``ask_api.cu`` (host driver), ``ask_kernels.cu`` (exhaustive and ASK
-  kernels) and ``ask_noalloc.cu`` (the allocation-free ASK entry point) as
-  ordinary whole-program device code;
+  kernels), ``ask_schemes.cu`` (the paper's SBR / MBR mappings),
+  ``ask_fp64.cu`` (double-precision kernels for deep zooms) and
+  ``ask_noalloc.cu`` (the allocation-free ASK entry point) as ordinary
+  whole-program device code;
 * ``ask_cdp2.cu`` with relocatable device code, device-linked against the
   CUDA device runtime (``cudadevrt``) for the tail-launch variant.
 
@@ -28,7 +30,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                       "-Xcompiler", "-ffp-contract=off", "--fmad=false", "-ftz=false",
                       "-prec-div=true", "-prec-sqrt=true", "-I", INCLUDE]
-PLAIN_UNITS = ["ask_api.cu", "ask_kernels.cu", "ask_schemes.cu", "ask_noalloc.cu"]
+PLAIN_UNITS = ["ask_api.cu", "ask_kernels.cu", "ask_schemes.cu", "ask_noalloc.cu", "ask_fp64.cu"]
 RDC_UNITS = ["ask_cdp2.cu"]
 
 

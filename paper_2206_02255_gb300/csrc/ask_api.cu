@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "ask_fp64.h"
 #include "ask_internal.h"
 
 // Device scratch of a batch render (owned by a context, or by a graph).
@@ -1327,3 +1328,168 @@ ask_status ask_check(ask_ctx *ctx, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Double precision (deep zooms): the exhaustive method and ASK with the
+// arithmetic of ask_fp64.cu, on the context's region tables and counters.
+// ---------------------------------------------------------------------------
+namespace {
+
+bool window64_ok(const ask_window64 *w)
+{
+    return w && std::isfinite(w->re_min) && std::isfinite(w->re_max) && std::isfinite(w->im_min) &&
+           std::isfinite(w->im_max) && w->re_max > w->re_min && w->im_max > w->im_min;
+}
+
+PixelMap64 pixel_map64(const ask_window64 *w, uint32_t n)
+{
+    PixelMap64 pm;
+    pm.re_min = w->re_min;
+    pm.im_min = w->im_min;
+    // double subtraction and division, each rounded once
+    const double wr = w->re_max - w->re_min;
+    const double wi = w->im_max - w->im_min;
+    pm.dx = wr / (double)n;
+    pm.dy = wi / (double)n;
+    return pm;
+}
+
+ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *window, uint32_t n,
+                         uint32_t max_dwell, const ask_params &p, uint32_t *d_dwell, cudaStream_t s,
+                         ask_stats *stats)
+{
+    const bool count = (p.flags & ASK_FLAG_COUNT) != 0;
+    const PixelMap64 pm = pixel_map64(window, n);
+    ask_status st;
+    cudaError_t e;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        if ((st = ensure_events(ctx)) != ASK_OK)
+            return st;
+    }
+    if ((st = ensure_counters(ctx)) != ASK_OK)
+        return st;
+    uint32_t launches = 0;
+    if (stats)
+        cudaEventRecord(ctx->ev[0], s);
+
+    if (method == ASK_METHOD_EXHAUSTIVE) {
+        if (count) {
+            if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, 0, 0, s)) != cudaSuccess)
+                return cuda_err(ctx, e, "init kernel");
+            ++launches;
+        }
+        if ((e = launch_exhaustive64(d_dwell, n, pm, max_dwell, p.block_x, p.block_y, count, ctx->ctr,
+                                     s)) != cudaSuccess)
+            return cuda_err(ctx, e, "double-precision exhaustive kernel");
+        ++launches;
+        if (stats) {
+            cudaEventRecord(ctx->ev[1], s);
+            if ((st = read_counters(ctx, s)) != ASK_OK)
+                return st;
+            cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[1]);
+            stats->iterations = count ? ctx->h_ctr->iterations : 0;
+            stats->kernel_launches = launches;
+        }
+        return ASK_OK;
+    }
+
+    LevelPlan plan;
+    if (!make_plan(n, p.g, p.r, p.B, &plan))
+        return set_err(ctx, ASK_EINVAL, "no valid subdivision plan for n=%u g=%u r=%u B=%u", n, p.g, p.r, p.B);
+    for (uint32_t i = 0; i < plan.levels; ++i)
+        plan.chunks[i] = 1u;  // one warp per region: no chunked-query state
+    if ((st = reserve_ask(ctx, plan)) != ASK_OK)
+        return st;
+    const uint32_t L = plan.levels;
+    if ((e = launch_init(ctx->olt[0], nullptr, ctx->ctr, n, plan.side[0], plan.axis0, 0, plan.axis0, s)) !=
+        cudaSuccess)
+        return cuda_err(ctx, e, "init kernel");
+    ++launches;
+    if (stats)
+        cudaEventRecord(ctx->ev[1], s);
+    for (uint32_t i = 0; i < L; ++i) {
+        Level64Args a;
+        a.map = d_dwell;
+        a.n = n;
+        a.pm = pm;
+        a.max_dwell = max_dwell;
+        a.level = i;
+        a.split = plan.split[i];
+        a.child_side = ceil_div(plan.side[i], p.r);
+        a.r = p.r;
+        a.olt_in = ctx->olt[i & 1];
+        a.olt_out = ctx->olt[(i + 1) & 1];
+        a.olt_cap = (uint32_t)ctx->olt_cap;
+        a.leaves = ctx->leaves;
+        a.leaf_cap = (uint32_t)ctx->leaf_cap;
+        a.ctr = ctx->ctr;
+        if ((e = launch_level64(a, count, ctx->dev.sms, s)) != cudaSuccess)
+            return cuda_err(ctx, e, "double-precision level kernel");
+        ++launches;
+        if (stats)
+            cudaEventRecord(ctx->ev[2 + i], s);
+    }
+    Leaf64Args la;
+    la.map = d_dwell;
+    la.n = n;
+    la.pm = pm;
+    la.max_dwell = max_dwell;
+    la.leaves = ctx->leaves;
+    la.leaf_cap = (uint32_t)ctx->leaf_cap;
+    la.ctr = ctx->ctr;
+    if ((e = launch_leaf64(la, count, ctx->dev.sms, s)) != cudaSuccess)
+        return cuda_err(ctx, e, "double-precision leaf kernel");
+    ++launches;
+    if (stats) {
+        cudaEventRecord(ctx->ev[2 + L], s);
+        if ((st = read_counters(ctx, s)) != ASK_OK)
+            return st;
+        cudaEventElapsedTime(&stats->ms_total, ctx->ev[0], ctx->ev[2 + L]);
+        for (uint32_t i = 0; i < L; ++i)
+            cudaEventElapsedTime(&stats->ms_per_level[i], ctx->ev[1 + i], ctx->ev[2 + i]);
+        cudaEventElapsedTime(&stats->ms_leaf, ctx->ev[1 + L], ctx->ev[2 + L]);
+        const DevCounters &c = *ctx->h_ctr;
+        stats->levels = L;
+        for (uint32_t i = 0; i < L; ++i) {
+            stats->regions_per_level[i] = c.count[i];
+            stats->fills_per_level[i] = c.fills[i];
+            stats->subdivisions_per_level[i] = c.subdivs[i];
+            stats->iterations_per_level[i] = c.level_iters[i];
+        }
+        stats->leaves = c.leaf_count;
+        stats->fill_pixels = c.fill_pixels;
+        stats->leaf_pixels = c.leaf_pixels;
+        stats->iterations = c.iterations;
+        stats->leaf_iterations = c.leaf_iters;
+        stats->kernel_launches = launches;
+    }
+    return ASK_OK;
+}
+
+}  // namespace
+
+extern "C" ask_status ask_render64(ask_ctx *ctx, ask_method method, const ask_window64 *window,
+                                   uint32_t n, uint32_t max_dwell, const ask_params *params,
+                                   uint32_t *d_dwell, void *stream, ask_stats *stats)
+{
+    if (!ctx)
+        return ASK_EINVAL;
+    if (!window64_ok(window))
+        return set_err(ctx, ASK_EINVAL, "window must be finite with min < max");
+    if (method == ASK_METHOD_CDP2)
+        return set_err(ctx, ASK_EINVAL, "ask_render64: CDP2 has no double-precision variant");
+    // the float window only stands in for the argument checks of the rest
+    const ask_window unit = {0.0f, 1.0f, 0.0f, 1.0f};
+    ask_params eff;
+    ask_status st = check_args(ctx, method, &unit, n, max_dwell, params, &eff);
+    if (st != ASK_OK)
+        return st;
+    if (eff.flags & ~ASK_FLAG_COUNT)
+        return set_err(ctx, ASK_EINVAL, "ask_render64 accepts ASK_FLAG_COUNT only (flags 0x%x)", eff.flags);
+    if (!d_dwell || ((uintptr_t)d_dwell & 15u))
+        return set_err(ctx, ASK_EINVAL, "d_dwell must be a non-NULL 16-byte aligned device pointer");
+    if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
+        return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
+    return render64_impl(ctx, method, window, n, max_dwell, eff, d_dwell, (cudaStream_t)stream, stats);
+}

@@ -133,3 +133,41 @@ def serving_requests(count=2000, seed=7, rate=200.0, sides=(256, 4096), zooms=(1
         md = rng.randint(*dwells)
         out.append(dict(id=k, t=t, window=_zoom_window(c, zoom), n=n, max_dwell=md, zoom=zoom))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Deep zooms, rendered in double precision: square windows of a power-of-two
+# width around points near the set's boundary, far past the zoom of 1e4 over
+# the 2 x 2 window at which single precision stops separating the pixels of
+# a large map.  (centre re, centre im, width, dwell cap)
+# ---------------------------------------------------------------------------
+DEEP_SPOTS = (
+    ("spiral_2^-28", -0.10109636384562, 0.95628651080914, 2.0 ** -28, 1024),
+    ("seahorse_2^-30", -0.743643887037151, 0.13182590420533, 2.0 ** -30, 4096),
+    ("antenna_2^-20", -1.25066, 0.02012, 2.0 ** -20, 2048),
+)
+
+
+def deep_window(name):
+    """(window, max_dwell) of a DEEP_SPOTS entry; the window's lower-left
+    corner is the listed point, so its sides are exact doubles."""
+    for nm, re0, im0, w, md in DEEP_SPOTS:
+        if nm == name:
+            return (re0, re0 + w, im0, im0 + w), md
+    raise KeyError(name)
+
+
+def deep_frames(count=16, seed=3, sides=(256, 2048), zooms=(1e5, 1e10), dwells=(512, 4096)):
+    """Seeded deep-zoom frames for the double-precision path: centre drawn
+    from the boundary centres, zoom log-uniform in `zooms` (relative to the
+    2 x 2 window), side uniform in `sides`, dwell cap log-uniform."""
+    rng = random.Random(seed)
+    centers = boundary_centers()
+    out = []
+    for _ in range(count):
+        n = rng.randint(*sides)
+        c = rng.choice(centers)
+        zoom = _log_uniform(rng, *zooms)
+        md = int(round(_log_uniform(rng, *dwells)))
+        out.append(dict(window=_zoom_window(c, zoom), n=n, max_dwell=md, zoom=zoom))
+    return out
