@@ -77,11 +77,13 @@ def parse():
     ap.add_argument("--max-dwell", type=int, default=None)
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the exhaustive and CDP2 comparison arms")
-    ap.add_argument("--workload", default="single", choices=["single", "large", "batch", "serve"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "large", "batch", "serve", "deep"],
                     help="single: one n=16384 map per step (default); large: one n=65536, "
                          "dwell 4096 map (17.2 GB) per step, tuned ASK vs exhaustive; batch: "
                          "256 frames of mixed size and zoom per step; serve: Poisson render "
-                         "requests")
+                         "requests; deep: one n=8192 double-precision map of a 2^-30 wide "
+                         "seahorse-valley window per step")
     ap.add_argument("--frames", type=int, default=256, help="batch: frames per step")
     return ap.parse_args()
 
@@ -752,6 +754,145 @@ def run_serve(args):
     ctx.close()
 
 
+# ---------------------------------------------------------------------------
+# Deep zoom: one double-precision map per step
+# ---------------------------------------------------------------------------
+# FP64-pipe operations per update in ask_fp64.cu: 3 DFMA + 1 DADD (the |z|^2
+# test is amortised over a block of updates)
+FP64_OPS_PER_ITER = 4
+# Nominal FP64 rate of the GB300 table (1.25 TFLOP/s with an FMA as 2 flops):
+# 625 G FP64-pipe lane operations per second.  No measured FP64 peak exists.
+FP64_PEAK_GOPS = 1.25e3 / 2
+
+
+def run_deep(args):
+    import torch
+
+    from paper_2206_02255_gb300 import ask, build, inputs
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    ctx = ask.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    spot = "seahorse_2^-30"
+    win, M = inputs.deep_window(spot)
+    n = args.n or 8192
+    M = args.max_dwell or M
+    out = torch.empty((n, n), dtype=torch.int32, device=dev)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(world, e0.elapsed_time(e1) / steps, dev)
+
+    # untimed tune: one warp per region at every level, so g runs higher
+    # than in single precision
+    cands = [(args.g, args.r, args.B)] if args.no_tune else \
+        [(g, r, B) for g in (32, 64, 128) for r in (2, 4) for B in (8, 16, 32)]
+    best = None
+    for g, r, B in cands:
+        p = ask.make_params(g, r, B)
+        ms = timed(lambda: ctx.render64("ask", win, n, M, p, out=out), 1, 1)
+        if best is None or ms < best[0]:
+            best = (ms, g, r, B)
+    _, g, r, B = best
+    p = ask.make_params(g, r, B)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_ask = timed(lambda: ctx.render64("ask", win, n, M, p, out=out), args.steps,
+                   max(3, args.warmup))
+    clk = clocks.stop()
+    ask_map = out.clone()
+    ex_out = torch.empty_like(out)
+    ms_ex = timed(lambda: ctx.render64("exhaustive", win, n, M, None, out=ex_out),
+                  max(2, args.steps // 4), 1)
+    ex_iters = int(ex_out.to(torch.int64).sum().item())      # exhaustive-equivalent work
+    mism = int((ask_map != ex_out).sum().item())
+    _, cst = ctx.render64("ask", win, n, M, ask.make_params(g, r, B, flags=ask.FLAG_COUNT),
+                          out=out, stats=True)
+    # per-kernel device times (CUDA events around each launch), mean of 3 renders
+    runs = [ctx.render64("ask", win, n, M, p, out=out, stats=True)[1] for _ in range(3)]
+    leaf_ms = sum(st["ms_leaf"] for st in runs) / len(runs)
+    level_ms = [sum(st["ms_per_level"][i] for st in runs) / len(runs) for i in range(runs[0]["levels"])]
+
+    # end to end: render into device memory, map copied to pinned host memory
+    host = torch.empty((n, n), dtype=torch.int32, pin_memory=True)
+    k_e2e = max(2, args.steps // 2)
+    ctx.render64("ask", win, n, M, p, out=out)
+    host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.render64("ask", win, n, M, p, out=out)
+        host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / k_e2e, dev)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        # the same window at n = 1024, rendered again until about 10 s have passed
+        n_cpu, g_cpu, reps = 1024, max(1, g * 1024 // n), 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 10.0 and reps < 200:
+            oracle.render_ms(win, n_cpu, M, g_cpu, r, B, fp64=True)
+            reps += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": reps * n_cpu * n_cpu / dt / 1e9, "unit": UNIT,
+               "cores": oracle.default_threads(), "kind": "oracle",
+               "sample": "%d double-precision Mariani-Silver maps of the same window at n=%d "
+                         "(g=%d r=%d B=%d), %.1f s" % (reps, n_cpu, g_cpu, r, B, dt)}
+
+    if rank == 0:
+        gp = lambda ms: world * n * n / (ms / 1e3) / 1e9
+        leaf_gops = cst["leaf_iterations"] * FP64_OPS_PER_ITER / (leaf_ms / 1e3) / 1e9
+        ex_gops = ex_iters * FP64_OPS_PER_ITER / (ms_ex / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": gp(ms_ask), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_ask,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "mandelbrot_fp64_%s_n%d_d%d" % (spot, n, M), "window": list(win),
+                       "zoom": 2.0 / (win[1] - win[0]), "n": n, "max_dwell": M,
+                       "g": g, "r": r, "B": B, "method": "ask_render64",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "%.0f MB map > 129 MB L2" % (4 * n * n / 1e6)},
+            "exhaustive64": {"ms": ms_ex, "gpix_s": gp(ms_ex),
+                             "fp64_gops": ex_gops, "frac_of_nominal_fp64": ex_gops / FP64_PEAK_GOPS},
+            "speedup_vs_exhaustive": ms_ex / ms_ask,
+            "dwell_iter_s": {"executed": cst["iterations"] / (ms_ask / 1e3),
+                             "exhaustive_equivalent": ex_iters / (ms_ask / 1e3)},
+            "mismatch_vs_exhaustive_pixels": mism,
+            "levels": cst["levels"], "leaves": cst["leaves"],
+            "ms_per_level": level_ms, "ms_leaf": leaf_ms,
+            "roofline": {"bound": "alu", "kernel": "leaf64_kernel", "achieved": leaf_gops,
+                         "peak": FP64_PEAK_GOPS, "unit": "G FP64-pipe ops/s",
+                         "frac": leaf_gops / FP64_PEAK_GOPS, "traffic": None,
+                         "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2 flops); no measured "
+                                        "FP64 peak",
+                         "work": "leaf pixels' dwells x %d FP64 ops / mean leaf-kernel time" %
+                                 FP64_OPS_PER_ITER},
+            "cpu_baseline": cpu,
+            "e2e": {"value": gp(t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 4 * n * n, "ms_per_step": 1e3 * t_e2e},
+            "gpu_launches": (2 + cst["levels"]) * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -760,6 +901,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "deep":
+        run_deep(args)
     else:
         run_gpu(args)
 

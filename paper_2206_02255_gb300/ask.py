@@ -237,6 +237,19 @@ def make_params(g=16, r=2, B=32, block=(16, 16), flags=0):
     return Params(g, r, B, block[0], block[1], flags)
 
 
+# Zoom (relative to the 2 x 2 window of the paper's configuration) past
+# which frames are rendered in double precision: at zoom 1e4 a window is
+# 2e-4 wide, and a map of a few thousand pixels has a spacing near one float
+# ulp of c, so neighbouring pixels start to share c in single precision.
+FP64_ZOOM = 1e4
+
+
+def needs_fp64(window):
+    """True for a window zoomed past FP64_ZOOM (narrower than 2 / FP64_ZOOM)."""
+    re0, re1, im0, im1 = (float(v) for v in window)
+    return max(re1 - re0, im1 - im0) < 2.0 / FP64_ZOOM
+
+
 def _method(m):
     return METHODS[m] if isinstance(m, str) else int(m)
 

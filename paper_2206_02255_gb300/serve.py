@@ -12,6 +12,10 @@ slot's copy stream while the next batch renders.  Requests that arrive
 while batches run wait for the next free slot.  A request's latency runs
 from its arrival to the moment its map is in host memory.
 
+Requests zoomed past ``ask.FP64_ZOOM`` are rendered in double precision
+(``ask_render64``) on the same compute stream, after their batch's
+single-precision frames.
+
 The baseline, :func:`serve_per_frame`, renders the same requests one at a
 time, in arrival order, with the single-frame ASK call.
 """
@@ -122,8 +126,12 @@ class Server:
                 q.dbuf, q.out = self.dpool.get(q.n)
                 q.hbuf, q.host = self.pool.get(q.n)
             frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r, B=q.B,
-                           out=q.out) for q in reqs]
-            self.ctxs[slot].render_batch(frames, stream=c)
+                           out=q.out) for q in reqs if not ask.needs_fp64(q.window)]
+            if frames:
+                self.ctxs[slot].render_batch(frames, stream=c)
+            for q in reqs:
+                if ask.needs_fp64(q.window):
+                    render_one(self.ctxs[slot], q, c)
             rendered = torch.cuda.Event()
             rendered.record(c)
         s.wait_event(rendered)
@@ -184,6 +192,16 @@ class Server:
         return requests
 
 
+def render_one(ctx, q, stream):
+    """Render request q alone into q.out on `stream`: single-frame ASK, in
+    double precision past ask.FP64_ZOOM."""
+    p = ask.make_params(q.g, q.r, q.B)
+    if ask.needs_fp64(q.window):
+        ctx.render64("ask", q.window, q.n, q.max_dwell, p, out=q.out, stream=stream)
+    else:
+        ctx.render("ask", q.window, q.n, q.max_dwell, p, out=q.out, stream=stream)
+
+
 def serve_per_frame(ctx, requests, poll_s=0.0002, pool=None, keep=True, dpool=None):
     """Baseline: one request at a time in arrival order, single-frame ASK,
     map copied to pinned host memory; returns requests with t_done set."""
@@ -198,8 +216,7 @@ def serve_per_frame(ctx, requests, poll_s=0.0002, pool=None, keep=True, dpool=No
         with torch.cuda.stream(s):
             q.dbuf, q.out = dpool.get(q.n)
             q.hbuf, q.host = pool.get(q.n)
-            ctx.render("ask", q.window, q.n, q.max_dwell, ask.make_params(q.g, q.r, q.B),
-                       out=q.out, stream=s)
+            render_one(ctx, q, s)
             q.host.copy_(q.out, non_blocking=True)
         s.synchronize()
         q.t_done = time.perf_counter() - t0

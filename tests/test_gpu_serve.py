@@ -37,3 +37,30 @@ def test_served_results_equal_alone(ctx, asklib):
         assert q.t_done >= q.t
     s = serve.summarize(rs)
     assert s["requests"] == 48 and s["p50_ms"] <= s["p99_ms"]
+
+
+def test_served_deep_zooms_render_in_double(ctx, asklib):
+    """Requests zoomed past 1e4 are served in double precision: in a mix with
+    single-precision requests, each deep map equals the request rendered
+    alone by ask_render64, each other map the request rendered by ask_render."""
+    from paper_2206_02255_gb300 import serve
+    shallow = inputs.serving_requests(count=12, seed=11, rate=4000.0, sides=(256, 700),
+                                      dwells=(256, 1024))
+    deep = inputs.deep_frames(count=8, seed=5, sides=(200, 600), dwells=(256, 2048))
+    mixed = []
+    for k in range(20):
+        d = dict(shallow[k // 2]) if k % 2 == 0 or k // 2 >= len(deep) else dict(deep[k // 2])
+        d["id"], d["t"] = k, 0.0005 * k
+        mixed.append(d)
+    assert sum(asklib.needs_fp64(d["window"]) for d in mixed) >= 6
+    srv = serve.Server(device=0, slots=2, budget_bytes=4 * 2 ** 20)
+    rs = [serve.Request(d, 8, 2, 16) for d in mixed]
+    srv.run(rs)
+    srv.close()
+    p = asklib.make_params(8, 2, 16)
+    for q in rs:
+        if asklib.needs_fp64(q.window):
+            alone = ctx.render64("ask", q.window, q.n, q.max_dwell, p)
+        else:
+            alone = ctx.render("ask", q.window, q.n, q.max_dwell, p)
+        assert np.array_equal(q.host.numpy().view(np.uint32), alone.cpu().numpy().view(np.uint32)), q.id
