@@ -16,7 +16,8 @@ zooms); this module only marshals numpy buffers.  Functions:
   sampled parity checks on maps too large to render on the CPU;
 * :func:`dwell64`, :func:`pixel_to_c64`, :func:`render_exhaustive64`,
   :func:`render_ms64` -- the same in double precision (deep zooms), the
-  window given in double.
+  window given in double; with the flag ``FLOAT_FLOAT`` the maps iterate in
+  float-float arithmetic instead (:func:`dwell_ff`).
 
 :class:`Oracle` wraps one build of the library; the module-level functions
 use the default build.  Tests also load deliberately broken builds through
@@ -31,6 +32,7 @@ from . import build as _build
 
 ESCAPE_LE = 1
 NO_FILL = 2
+FLOAT_FLOAT = 4
 REGION_FILL, REGION_SUBDIVIDE, REGION_LEAF = 0, 1, 2
 MAX_LEVELS = 32
 
@@ -110,6 +112,8 @@ class Oracle:
         f64 = ctypes.c_double
         L.oracle_dwell64.restype = u32
         L.oracle_dwell64.argtypes = [f64, f64, u32, u32]
+        L.oracle_dwell_ff.restype = u32
+        L.oracle_dwell_ff.argtypes = [f64, f64, u32, u32]
         L.oracle_pixel_to_c64.restype = None
         L.oracle_pixel_to_c64.argtypes = [P(Window64), u32, u32, u32, P(f64), P(f64)]
         L.oracle_render_exhaustive64.restype = ctypes.c_int
@@ -141,6 +145,10 @@ class Oracle:
     def dwell64(self, cr, ci, max_dwell, flags=0):
         """Dwell of the point c = cr + i*ci in double precision."""
         return int(self.lib.oracle_dwell64(cr, ci, max_dwell, flags))
+
+    def dwell_ff(self, cr, ci, max_dwell, flags=0):
+        """Dwell of c (given in double) in float-float arithmetic."""
+        return int(self.lib.oracle_dwell_ff(cr, ci, max_dwell, flags))
 
     def pixel_to_c64(self, window, n, px, py):
         """The double-precision point sampled by pixel (px, py)."""
@@ -254,6 +262,10 @@ def render_ms_region(*a, **k):
 
 def dwell64(*a, **k):
     return default().dwell64(*a, **k)
+
+
+def dwell_ff(*a, **k):
+    return default().dwell_ff(*a, **k)
 
 
 def pixel_to_c64(*a, **k):

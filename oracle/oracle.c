@@ -31,7 +31,8 @@
  *       zi' = fmaf(zr + zr, zi, ci);                    -- 2 zr zi + ci
  *     and, for deep zooms where single precision cannot separate
  *     neighbouring pixels, the same sequence with every operation rounded
- *     once to double (the *64 functions, window given in double);
+ *     once to double (the *64 functions, window given in double), or in
+ *     float-float arithmetic (ORACLE_FLOAT_FLOAT, see oracle_dwell_ff);
  *   - pixel (px, py) samples c at its corner:
  *       dx = (re_max - re_min) / n, dy = (im_max - im_min) / n  (float)
  *       cr = fmaf(px, dx, re_min), ci = fmaf(py, dy, im_min)
@@ -101,6 +102,94 @@ uint32_t oracle_dwell64(double cr, double ci, uint32_t max_dwell, uint32_t flags
     return d;
 }
 
+/* The same iteration in float-float ("double-single") arithmetic, a value
+ * being the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2.
+ * It carries about 48 significant bits using single-precision operations
+ * only, for GPUs whose single-precision rate is many times their
+ * double-precision rate.  Building blocks, each float operation rounded once:
+ *   TwoSum(a, b) (Knuth): s = a + b and the exact error of that sum;
+ *   Fast2Sum(a, b) (Dekker): the same in 3 operations when |a| >= |b|;
+ *   the exact error of a product a*b, as fma(a, b, -a*b).
+ * On them (Dekker's products; the "sloppy" sum, whose error is bounded
+ * relative to the operands rather than to the result, which suffices here
+ * since |z| and |c| stay near 2 while the orbit is tested):
+ *   add(x, y):  (s, e) = TwoSum(xh, yh); w = e + (xl + yl); Fast2Sum(s, w)
+ *   mul(x, y):  p = xh*yh; e = fma(xh, yh, -p); e = fma(xh, yl, e);
+ *               e = fma(xl, yh, e); Fast2Sum(p, e)
+ *   sqr(x):     p = xh*xh; e = fma(xh, xh, -p); e = fma(xh + xh, xl, e);
+ *               Fast2Sum(p, e)
+ * One iteration: zr2 = sqr(zr), zi2 = sqr(zi); continue while
+ * zr2.hi + zi2.hi < 4; zr' = add(zr2, add(cr, -zi2)); zi' = add(2 mul(zr, zi), ci)
+ * (negation and doubling are exact on both halves). */
+typedef struct {
+    float hi, lo;
+} ff_t;
+
+static ff_t ff_fast_two_sum(float a, float b)
+{
+    ff_t r;
+    r.hi = a + b;
+    r.lo = b - (r.hi - a);
+    return r;
+}
+
+static ff_t ff_add(ff_t x, ff_t y)
+{
+    float s = x.hi + y.hi;
+    float bb = s - x.hi;
+    float e = (x.hi - (s - bb)) + (y.hi - bb);
+    float w = e + (x.lo + y.lo);
+    return ff_fast_two_sum(s, w);
+}
+
+static ff_t ff_mul(ff_t x, ff_t y)
+{
+    float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return ff_fast_two_sum(p, e);
+}
+
+static ff_t ff_sqr(ff_t x)
+{
+    float p = x.hi * x.hi;
+    float e = fmaf(x.hi, x.hi, -p);
+    e = fmaf(x.hi + x.hi, x.lo, e);
+    return ff_fast_two_sum(p, e);
+}
+
+static ff_t ff_from_double(double v)
+{
+    ff_t r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+
+uint32_t oracle_dwell_ff(double cr_d, double ci_d, uint32_t max_dwell, uint32_t flags)
+{
+    const ff_t cr = ff_from_double(cr_d), ci = ff_from_double(ci_d);
+    ff_t zr = {0.0f, 0.0f}, zi = {0.0f, 0.0f};
+    uint32_t d = 0;
+    while (d < max_dwell) {
+        ff_t zr2 = ff_sqr(zr), zi2 = ff_sqr(zi);
+        float m = zr2.hi + zi2.hi;
+        int bounded = (flags & ORACLE_ESCAPE_LE) ? (m <= 4.0f) : (m < 4.0f);
+        if (!bounded)
+            break;
+        ff_t neg_zi2 = {-zi2.hi, -zi2.lo};
+        ff_t nzr = ff_add(zr2, ff_add(cr, neg_zi2));
+        ff_t p = ff_mul(zr, zi);
+        ff_t p2 = {p.hi + p.hi, p.lo + p.lo};
+        ff_t nzi = ff_add(p2, ci);
+        zr = nzr;
+        zi = nzi;
+        d++;
+    }
+    return d;
+}
+
 /* Pixel -> point of the complex plane (corner sampling, see header). */
 void oracle_pixel_to_c(const oracle_window *win, uint32_t n, uint32_t px,
                        uint32_t py, float *cr, float *ci)
@@ -133,6 +222,8 @@ static uint32_t pixel_dwell(const any_window *win, uint32_t n,
     if (win->w64) {
         double cr, ci;
         oracle_pixel_to_c64(win->w64, n, px, py, &cr, &ci);
+        if (flags & ORACLE_FLOAT_FLOAT)
+            return oracle_dwell_ff(cr, ci, max_dwell, flags);
         return oracle_dwell64(cr, ci, max_dwell, flags);
     }
     float cr, ci;

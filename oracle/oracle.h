@@ -18,6 +18,9 @@ extern "C" {
 /* flags */
 #define ORACLE_ESCAPE_LE 1u /* continue while |z|^2 <= 4 instead of < 4 */
 #define ORACLE_NO_FILL 2u   /* never fill: every region ends as a leaf */
+/* Double-precision windows only: iterate in float-float arithmetic
+ * (oracle_dwell_ff) instead of binary64. */
+#define ORACLE_FLOAT_FLOAT 4u
 
 /* region kinds in the log */
 #define ORACLE_REGION_FILL 0u
@@ -70,6 +73,10 @@ int oracle_initial_region(uint32_t n, uint32_t g, uint32_t gx, uint32_t gy,
 uint32_t oracle_dwell64(double cr, double ci, uint32_t max_dwell, uint32_t flags);
 void oracle_pixel_to_c64(const oracle_window64 *win, uint32_t n, uint32_t px,
                          uint32_t py, double *cr, double *ci);
+/* Dwell in float-float arithmetic: each value is an unevaluated sum hi + lo
+ * of two floats (about 48 significant bits), every float operation rounded
+ * once; c = (cr, ci) is split as hi = (float)c, lo = (float)(c - hi). */
+uint32_t oracle_dwell_ff(double cr, double ci, uint32_t max_dwell, uint32_t flags);
 int oracle_render_exhaustive64(const oracle_window64 *win, uint32_t n,
                                uint32_t max_dwell, uint32_t flags, uint32_t *out,
                                int nthreads, uint64_t *iterations);

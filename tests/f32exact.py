@@ -139,3 +139,62 @@ def exhaustive64(window, n, max_dwell):
             cr, ci = pixel_c64(window, n, px, py)
             out[py][px] = dwell64(cr, ci, max_dwell)
     return out
+
+
+# --------------------------------------------------------------------------
+# float-float: a value is (hi, lo), two float32 values; every float
+# operation below is rounded once (rn32), the fused multiply-adds included
+# --------------------------------------------------------------------------
+def _fast_two_sum(a, b):
+    s = rn32(a + b)
+    return s, rn32(b - rn32(s - a))
+
+
+def _two_sum(a, b):
+    s = rn32(a + b)
+    bb = rn32(s - a)
+    return s, rn32(rn32(a - rn32(s - bb)) + rn32(b - bb))
+
+
+def ff_add(x, y):
+    s, e = _two_sum(x[0], y[0])
+    return _fast_two_sum(s, rn32(e + rn32(x[1] + y[1])))
+
+
+def ff_mul(x, y):
+    p = rn32(x[0] * y[0])
+    e = rn32(x[0] * y[0] - p)
+    e = rn32(x[0] * y[1] + e)
+    e = rn32(x[1] * y[0] + e)
+    return _fast_two_sum(p, e)
+
+
+def ff_sqr(x):
+    p = rn32(x[0] * x[0])
+    e = rn32(x[0] * x[0] - p)
+    e = rn32(rn32(x[0] + x[0]) * x[1] + e)
+    return _fast_two_sum(p, e)
+
+
+def ff_from_double(v):
+    v = f64(v)
+    hi = rn32(v)
+    return hi, rn32(v - hi)
+
+
+def dwell_ff(cr, ci, max_dwell, le=False):
+    """Dwell in float-float arithmetic with c given in double."""
+    cr, ci = ff_from_double(cr), ff_from_double(ci)
+    zr = zi = (Fraction(0), Fraction(0))
+    d = 0
+    while d < max_dwell:
+        zr2, zi2 = ff_sqr(zr), ff_sqr(zi)
+        m = rn32(zr2[0] + zi2[0])
+        if not (m <= 4 if le else m < 4):
+            break
+        nzr = ff_add(zr2, ff_add(cr, (-zi2[0], -zi2[1])))
+        p = ff_mul(zr, zi)
+        nzi = ff_add((2 * p[0], 2 * p[1]), ci)
+        zr, zi = nzr, nzi
+        d += 1
+    return d

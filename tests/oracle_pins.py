@@ -360,8 +360,64 @@ def pin_ms64_invariants(orc):
         assert st["fills_per_level"] != [0] * len(st["fills_per_level"]), (n, g)
 
 
+# --------------------------------------------------------------------------
+# float-float (deep zooms on the single-precision pipe)
+# --------------------------------------------------------------------------
+FLOAT_FLOAT = 4
+SPIRAL_WINDOW = DEEP_WINDOW
+ANTENNA_WINDOW = (-1.25066, -1.25066 + 2.0 ** -20, 0.02012, 0.02012 + 2.0 ** -20)
+
+
+def pin_closed_forms_ff(orc):
+    """The hand-computed orbits are exact in float-float as well (every lo
+    part stays 0)."""
+    for cr, ci, M, flags, d in closed_forms():
+        assert orc.dwell_ff(cr, ci, M, flags) == d, (cr, ci, M, flags, d)
+
+
+def pin_exact_points_ff(orc):
+    """Random points, and deep-zoom points 1e-12 apart (float32 alone cannot
+    separate them), against an exact-rational evaluation of the float-float
+    operations (each float operation rounded once by rn32)."""
+    rng = random.Random(20220607)
+    for _ in range(60):
+        cr, ci = rng.uniform(-2.2, 1.0), rng.uniform(-1.4, 1.4)
+        assert orc.dwell_ff(cr, ci, 48) == f32exact.dwell_ff(cr, ci, 48), (cr, ci)
+    seen = set()
+    for k in range(10):
+        cr, ci = SPIRAL_WINDOW[0] + k * 1e-12, SPIRAL_WINDOW[2] + (k % 4) * 3e-12
+        d = orc.dwell_ff(cr, ci, 300)
+        assert d == f32exact.dwell_ff(cr, ci, 300), (cr, ci)
+        seen.add(d)
+    assert len(seen) > 1
+
+
+def pin_ff_tracks_double(orc):
+    """Float-float carries about 48 bits, so at zooms of 1e6 to 1e9 its maps
+    agree with the binary64 maps except near escape thresholds, where the
+    orbit is chaotic: at least 97% of the pixels are equal, and the map
+    resolves what float32 cannot (many dwells along each row)."""
+    for win, n, M in [(SPIRAL_WINDOW, 48, 1024), (ANTENNA_WINDOW, 48, 2048)]:
+        ff = orc.render_exhaustive(win, n, M, flags=FLOAT_FLOAT, threads=2, fp64=True)
+        d64 = orc.render_exhaustive(win, n, M, threads=2, fp64=True)
+        assert (ff == d64).mean() >= 0.97, (win, (ff == d64).mean())
+        assert min(len(np.unique(ff[y])) for y in range(0, n, 7)) > 4
+
+
+def pin_ms_ff_invariants(orc):
+    """The recursion's invariants on float-float maps; with fills off it
+    equals the float-float exhaustive map."""
+    for win, n, M, g, r, B in [(SPIRAL_WINDOW, 64, 300, 4, 2, 4), (ANTENNA_WINDOW, 90, 800, 3, 3, 4)]:
+        ex = orc.render_exhaustive(win, n, M, flags=FLOAT_FLOAT, threads=2, fp64=True)
+        ms, st, log = orc.render_ms(win, n, M, g, r, B, flags=FLOAT_FLOAT, log=True, fp64=True)
+        check_region_log(ex, ms, st, log, n, g, r, B)
+        nf, _ = orc.render_ms(win, n, M, g, r, B, flags=FLOAT_FLOAT | NO_FILL, threads=2, fp64=True)
+        assert np.array_equal(nf, ex)
+
+
 ALL_PINS = [pin_closed_forms, pin_exact_points, pin_exact_tiny_maps,
             pin_c0_pixels, pin_symmetry_and_area, pin_no_fill_equals_exhaustive,
             pin_tree_by_hand, pin_ms_invariants, pin_uniform_windows, pin_stopping_side,
             pin_threads_and_regions, pin_closed_forms64, pin_exact_points64,
-            pin_exact_tiny_maps64, pin_deep_zoom64, pin_ms64_invariants]
+            pin_exact_tiny_maps64, pin_deep_zoom64, pin_ms64_invariants, pin_closed_forms_ff,
+            pin_exact_points_ff, pin_ff_tracks_double, pin_ms_ff_invariants]

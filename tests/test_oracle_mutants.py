@@ -48,6 +48,17 @@ MUTANTS = [
      "*ci = fma((double)py + 0.5, dy, win->im_min);"),
     ("map_in_float_64", "return oracle_dwell64(cr, ci, max_dwell, flags);",
      "return oracle_dwell((float)cr, (float)ci, max_dwell, flags);"),
+    # the float-float functions
+    ("ff_add_drops_lo", "float w = e + (x.lo + y.lo);", "float w = e;"),
+    ("ff_two_sum_sign", "float e = (x.hi - (s - bb)) + (y.hi - bb);",
+     "float e = (x.hi - (s - bb)) - (y.hi - bb);"),
+    ("ff_fast_two_sum_error", "r.lo = b - (r.hi - a);", "r.lo = b - r.hi;"),
+    ("ff_mul_drops_cross_term", "e = fmaf(x.lo, y.hi, e);", "e = e + 0.0f;"),
+    ("ff_sqr_single_cross_term", "e = fmaf(x.hi + x.hi, x.lo, e);", "e = fmaf(x.hi, x.lo, e);"),
+    ("ff_split_drops_lo", "r.lo = (float)(v - (double)r.hi);", "r.lo = 0.0f;"),
+    ("ff_wrong_sign_re", "ff_t neg_zi2 = {-zi2.hi, -zi2.lo};", "ff_t neg_zi2 = {zi2.hi, zi2.lo};"),
+    ("ff_test_uses_lo", "float m = zr2.hi + zi2.hi;", "float m = zr2.hi + zi2.lo;"),
+    ("ff_not_doubled", "ff_t p2 = {p.hi + p.hi, p.lo + p.lo};", "ff_t p2 = {p.hi + p.hi, p.lo};"),
 ]
 
 
