@@ -763,6 +763,11 @@ FP64_OPS_PER_ITER = 4
 # Nominal FP64 rate of the GB300 table (1.25 TFLOP/s with an FMA as 2 flops):
 # 625 G FP64-pipe lane operations per second.  No measured FP64 peak exists.
 FP64_PEAK_GOPS = 1.25e3 / 2
+# FP32 instructions per float-float update (ArithFF::update: two squares of
+# 7, three sums of 11, one product of 7, a doubling of 2)
+FF_OPS_PER_ITER = 56
+# FP32 pipe: 152 SMs x 128 lanes x 2070 MHz (operations per second, in G)
+FP32_PEAK_GOPS = 152 * 128 * 2.07
 
 
 def run_deep(args):
@@ -797,15 +802,18 @@ def run_deep(args):
 
     # untimed tune: one warp per region at every level, so g runs higher
     # than in single precision
-    cands = [(args.g, args.r, args.B)] if args.no_tune else \
-        [(g, r, B) for g in (32, 64, 128) for r in (2, 4) for B in (8, 16, 32)]
-    best = None
-    for g, r, B in cands:
-        p = ask.make_params(g, r, B)
-        ms = timed(lambda: ctx.render64("ask", win, n, M, p, out=out), 1, 1)
-        if best is None or ms < best[0]:
-            best = (ms, g, r, B)
-    _, g, r, B = best
+    def tune(flags):
+        cands = [(args.g, args.r, args.B)] if args.no_tune else \
+            [(g, r, B) for g in (32, 64, 128) for r in (2, 4) for B in (8, 16, 32)]
+        best = None
+        for g, r, B in cands:
+            p = ask.make_params(g, r, B, flags=flags)
+            ms = timed(lambda: ctx.render64("ask", win, n, M, p, out=out), 1, 1)
+            if best is None or ms < best[0]:
+                best = (ms, g, r, B)
+        return best[1:]
+
+    g, r, B = tune(0)
     p = ask.make_params(g, r, B)
 
     clocks = ClockSampler(local)
@@ -826,6 +834,19 @@ def run_deep(args):
     runs = [ctx.render64("ask", win, n, M, p, out=out, stats=True)[1] for _ in range(3)]
     leaf_ms = sum(st["ms_leaf"] for st in runs) / len(runs)
     level_ms = [sum(st["ms_per_level"][i] for st in runs) / len(runs) for i in range(runs[0]["levels"])]
+
+    # the same map in float-float arithmetic on the FP32 pipe
+    FF = ask.FLAG_FLOAT_FLOAT
+    gf, rf, Bf = tune(FF)
+    pff = ask.make_params(gf, rf, Bf, flags=FF)
+    ms_ff = timed(lambda: ctx.render64("ask", win, n, M, pff, out=out), args.steps, max(3, args.warmup))
+    ff_diff = int((out != ask_map).sum().item())
+    ms_ex_ff = timed(lambda: ctx.render64("exhaustive", win, n, M, ask.make_params(1, 2, 1, flags=FF),
+                                          out=ex_out), max(2, args.steps // 4), 1)
+    _, cff = ctx.render64("ask", win, n, M, ask.make_params(gf, rf, Bf, flags=FF | ask.FLAG_COUNT),
+                          out=out, stats=True)
+    runs_ff = [ctx.render64("ask", win, n, M, pff, out=out, stats=True)[1] for _ in range(3)]
+    leaf_ff_ms = sum(st["ms_leaf"] for st in runs_ff) / len(runs_ff)
 
     # end to end: render into device memory, map copied to pinned host memory
     host = torch.empty((n, n), dtype=torch.int32, pin_memory=True)
@@ -884,6 +905,19 @@ def run_deep(args):
                                         "FP64 peak",
                          "work": "leaf pixels' dwells x %d FP64 ops / mean leaf-kernel time" %
                                  FP64_OPS_PER_ITER},
+            "float_float": {
+                "flag": "ASK_FLAG_FLOAT_FLOAT", "g": gf, "r": rf, "B": Bf,
+                "ms": ms_ff, "gpix_s": gp(ms_ff), "speedup_vs_binary64": ms_ask / ms_ff,
+                "exhaustive_ms": ms_ex_ff, "speedup_vs_exhaustive": ms_ex_ff / ms_ff,
+                "pixels_differing_from_binary64": ff_diff,
+                "ms_leaf": leaf_ff_ms,
+                "leaf_roofline": {"bound": "alu", "achieved": cff["leaf_iterations"] * FF_OPS_PER_ITER /
+                                  (leaf_ff_ms / 1e3) / 1e9,
+                                  "peak": FP32_PEAK_GOPS, "unit": "G FP32-pipe ops/s",
+                                  "frac": cff["leaf_iterations"] * FF_OPS_PER_ITER /
+                                  (leaf_ff_ms / 1e3) / 1e9 / FP32_PEAK_GOPS,
+                                  "work": "leaf pixels' dwells x %d FP32 ops / mean leaf-kernel time"
+                                          % FF_OPS_PER_ITER}},
             "cpu_baseline": cpu,
             "e2e": {"value": gp(t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 4 * n * n, "ms_per_step": 1e3 * t_e2e},

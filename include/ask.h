@@ -118,6 +118,9 @@ typedef enum {
  * the next synchronising call returns ASK_EOVERFLOW and clears it.  The map
  * of such a render is incomplete. */
 #define ASK_FLAG_INJECT_OVERFLOW 512u
+/* ask_render64 only: iterate in float-float arithmetic on the FP32 pipe
+ * instead of binary64 (see ask_render64). */
+#define ASK_FLAG_FLOAT_FLOAT 1024u
 
 typedef struct {
     float re_min, re_max, im_min, im_max;
@@ -295,7 +298,14 @@ typedef struct {
  * Methods ASK_METHOD_EXHAUSTIVE and ASK_METHOD_ASK (same subdivision rule,
  * Sec. 4.2.1 and Sec. 5; one warp per region, so g should give a few
  * thousand initial regions); ASK_METHOD_CDP2 returns ASK_EINVAL.
- * params->flags: 0 or ASK_FLAG_COUNT.  Output, ownership, stream, stats and
+ * params->flags: ASK_FLAG_COUNT and ASK_FLAG_FLOAT_FLOAT.  With
+ * ASK_FLAG_FLOAT_FLOAT every value is the unevaluated sum hi + lo of two
+ * floats (about 48 significant bits) and the iteration runs on the FP32
+ * pipe, which GB300 runs 64 times faster than FP64: c from the double pixel
+ * map split as hi = (float)c, lo = (float)(c - hi); sums by TwoSum of the
+ * hi parts, plus the lo parts, then Fast2Sum; products and squares by
+ * Dekker's scheme with fma; the test zr^2.hi + zi^2.hi < 4.  Its maps
+ * differ from the binary64 maps only where the orbit is chaotic.  Output, ownership, stream, stats and
  * error behaviour as ask_render (ms_fill is 0: uniform regions are filled
  * by the level kernels). */
 ask_status ask_render64(ask_ctx *ctx, ask_method method, const ask_window64 *window,

@@ -29,6 +29,7 @@ FLAG_MBR = 64
 FLAG_STAGED_COPY = 128
 FLAG_SERIAL_FILL = 256
 FLAG_INJECT_OVERFLOW = 512
+FLAG_FLOAT_FLOAT = 1024
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 

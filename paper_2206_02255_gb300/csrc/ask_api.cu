@@ -1359,6 +1359,7 @@ ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *wi
                          ask_stats *stats)
 {
     const bool count = (p.flags & ASK_FLAG_COUNT) != 0;
+    const bool ff = (p.flags & ASK_FLAG_FLOAT_FLOAT) != 0;
     const PixelMap64 pm = pixel_map64(window, n);
     ask_status st;
     cudaError_t e;
@@ -1379,8 +1380,8 @@ ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *wi
                 return cuda_err(ctx, e, "init kernel");
             ++launches;
         }
-        if ((e = launch_exhaustive64(d_dwell, n, pm, max_dwell, p.block_x, p.block_y, count, ctx->ctr,
-                                     s)) != cudaSuccess)
+        if ((e = launch_exhaustive64(d_dwell, n, pm, max_dwell, p.block_x, p.block_y, count, ff,
+                                     ctx->ctr, s)) != cudaSuccess)
             return cuda_err(ctx, e, "double-precision exhaustive kernel");
         ++launches;
         if (stats) {
@@ -1424,7 +1425,7 @@ ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *wi
         a.leaves = ctx->leaves;
         a.leaf_cap = (uint32_t)ctx->leaf_cap;
         a.ctr = ctx->ctr;
-        if ((e = launch_level64(a, count, ctx->dev.sms, s)) != cudaSuccess)
+        if ((e = launch_level64(a, count, ff, ctx->dev.sms, s)) != cudaSuccess)
             return cuda_err(ctx, e, "double-precision level kernel");
         ++launches;
         if (stats)
@@ -1438,7 +1439,7 @@ ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *wi
     la.leaves = ctx->leaves;
     la.leaf_cap = (uint32_t)ctx->leaf_cap;
     la.ctr = ctx->ctr;
-    if ((e = launch_leaf64(la, count, ctx->dev.sms, s)) != cudaSuccess)
+    if ((e = launch_leaf64(la, count, ff, ctx->dev.sms, s)) != cudaSuccess)
         return cuda_err(ctx, e, "double-precision leaf kernel");
     ++launches;
     if (stats) {
@@ -1481,12 +1482,20 @@ extern "C" ask_status ask_render64(ask_ctx *ctx, ask_method method, const ask_wi
         return set_err(ctx, ASK_EINVAL, "ask_render64: CDP2 has no double-precision variant");
     // the float window only stands in for the argument checks of the rest
     const ask_window unit = {0.0f, 1.0f, 0.0f, 1.0f};
-    ask_params eff;
-    ask_status st = check_args(ctx, method, &unit, n, max_dwell, params, &eff);
+    ask_params eff, plain;
+    if (params) {
+        plain = *params;
+        plain.flags &= ~ASK_FLAG_FLOAT_FLOAT;  // a flag of this entry point only
+    }
+    ask_status st = check_args(ctx, method, &unit, n, max_dwell, params ? &plain : nullptr, &eff);
     if (st != ASK_OK)
         return st;
-    if (eff.flags & ~ASK_FLAG_COUNT)
-        return set_err(ctx, ASK_EINVAL, "ask_render64 accepts ASK_FLAG_COUNT only (flags 0x%x)", eff.flags);
+    if (params)
+        eff.flags = params->flags;
+    if (eff.flags & ~(ASK_FLAG_COUNT | ASK_FLAG_FLOAT_FLOAT))
+        return set_err(ctx, ASK_EINVAL,
+                       "ask_render64 accepts ASK_FLAG_COUNT and ASK_FLAG_FLOAT_FLOAT only (flags 0x%x)",
+                       eff.flags);
     if (!d_dwell || ((uintptr_t)d_dwell & 15u))
         return set_err(ctx, ASK_EINVAL, "d_dwell must be a non-NULL 16-byte aligned device pointer");
     if (cudaSetDevice(ctx->dev.device) != cudaSuccess)

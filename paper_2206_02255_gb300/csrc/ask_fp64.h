@@ -1,5 +1,5 @@
-// ask_fp64.h -- declarations of the double-precision (deep-zoom) kernels of
-// ask_fp64.cu, used by the host driver.  Not part of the ABI.
+// ask_fp64.h -- declarations of the deep-zoom kernels of ask_fp64.cu
+// (binary64 or float-float), used by the host driver.  Not part of the ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,11 +45,12 @@ struct Leaf64Args {
 };
 
 // count: accumulate z-updates (and pixel counts) in the counters, as
-// ASK_FLAG_COUNT does for the single-precision kernels.
+// ASK_FLAG_COUNT does for the single-precision kernels.  ff: float-float
+// arithmetic instead of binary64.
 cudaError_t launch_exhaustive64(uint32_t *map, uint32_t n, PixelMap64 pm, uint32_t max_dwell,
-                                uint32_t bx, uint32_t by, bool count, DevCounters *ctr,
+                                uint32_t bx, uint32_t by, bool count, bool ff, DevCounters *ctr,
                                 cudaStream_t s);
-cudaError_t launch_level64(const Level64Args &a, bool count, int sms, cudaStream_t s);
-cudaError_t launch_leaf64(const Leaf64Args &a, bool count, int sms, cudaStream_t s);
+cudaError_t launch_level64(const Level64Args &a, bool count, bool ff, int sms, cudaStream_t s);
+cudaError_t launch_leaf64(const Leaf64Args &a, bool count, bool ff, int sms, cudaStream_t s);
 
 }  // namespace ask
