@@ -17,7 +17,8 @@ SRC = os.path.join(os.path.dirname(HERE), "oracle")
 MUTANTS = [
     ("dropped_factor_two", "float nzi = fmaf(zr + zr, zi, ci);", "float nzi = fmaf(zr, zi, ci);"),
     ("wrong_sign_re", "float t = fmaf(-zi, zi, cr);", "float t = fmaf(zi, zi, cr);"),
-    ("escape_le", ": (m < 4.0f);", ": (m <= 4.0f);"),
+    ("escape_le", "float m = fmaf(zr, zr, zi2);\n        int bounded = (flags & ORACLE_ESCAPE_LE) ? (m <= 4.0f) : (m < 4.0f);",
+     "float m = fmaf(zr, zr, zi2);\n        int bounded = (flags & ORACLE_ESCAPE_LE) ? (m <= 4.0f) : (m <= 4.0f);"),
     ("check_after_update", "while (d < max_dwell) {\n        float zi2",
      "while (d < max_dwell) {\n        d++; if (d > max_dwell) break;\n        float zi2"),
     ("transposed_operand", "*ci = fmaf((float)py, dy, win->im_min);",
@@ -58,6 +59,8 @@ MUTANTS = [
     ("ff_split_drops_lo", "r.lo = (float)(v - (double)r.hi);", "r.lo = 0.0f;"),
     ("ff_wrong_sign_re", "ff_t neg_zi2 = {-zi2.hi, -zi2.lo};", "ff_t neg_zi2 = {zi2.hi, zi2.lo};"),
     ("ff_test_uses_lo", "float m = zr2.hi + zi2.hi;", "float m = zr2.hi + zi2.lo;"),
+    ("ff_escape_le", "float m = zr2.hi + zi2.hi;\n        int bounded = (flags & ORACLE_ESCAPE_LE) ? (m <= 4.0f) : (m < 4.0f);",
+     "float m = zr2.hi + zi2.hi;\n        int bounded = (flags & ORACLE_ESCAPE_LE) ? (m <= 4.0f) : (m <= 4.0f);"),
     ("ff_not_doubled", "ff_t p2 = {p.hi + p.hi, p.lo + p.lo};", "ff_t p2 = {p.hi + p.hi, p.lo};"),
 ]
 
