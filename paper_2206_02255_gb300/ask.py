@@ -404,21 +404,45 @@ class Context:
 
     def render_batch(self, frames, flags=0, stream=None, stats=False):
         """Render a batch of frames (see ``_frames``) with one launch chain.
-        Returns None, or the summed stats dict when ``stats`` (synchronises)."""
+        Frames zoomed past FP64_ZOOM (``needs_fp64``), whose windows a float
+        cannot hold, are rendered after it on the same stream, one
+        ``ask_render64`` (binary64 ASK) each.  Returns None, or, when
+        ``stats`` (synchronises), the stats dict summed over the
+        single-precision frames, with ``fp64_frames`` the number routed.
+        Frame numbers in the library's error messages count the
+        single-precision frames only."""
         import torch
-        arr = self._frames(frames)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        st_obj = Stats() if stats else None
-        st = lib().ask_render_batch(self._h, arr, len(frames), flags,
-                                    ctypes.c_void_p(s.cuda_stream),
-                                    ctypes.byref(st_obj) if st_obj is not None else None)
-        if st != OK:
-            self._raise(st, "ask_render_batch")
-        return st_obj.as_dict() if stats else None
+        shallow = [f for f in frames if not needs_fp64(f["window"])]
+        deep = [f for f in frames if needs_fp64(f["window"])]
+        out = None
+        if shallow or not deep:  # an empty batch is the library's argument error
+            arr = self._frames(shallow)
+            st_obj = Stats() if stats else None
+            st = lib().ask_render_batch(self._h, arr, len(shallow), flags,
+                                        ctypes.c_void_p(s.cuda_stream),
+                                        ctypes.byref(st_obj) if st_obj is not None else None)
+            if st != OK:
+                self._raise(st, "ask_render_batch")
+            out = st_obj.as_dict() if stats else None
+        for f in deep:
+            self.render64("ask", f["window"], int(f["n"]), int(f["max_dwell"]),
+                          make_params(int(f["g"]), int(f["r"]), int(f["B"])), out=f["out"],
+                          stream=s)
+        if stats:
+            if out is None:
+                s.synchronize()
+                out = Stats().as_dict()
+            out["fp64_frames"] = len(deep)
+        return out
 
     def graph_batch(self, frames, flags=0, stream=None):
-        """Capture a batch render as a CUDA graph (see :class:`Graph`)."""
+        """Capture a batch render as a CUDA graph (see :class:`Graph`).
+        Single-precision frames only: a frame zoomed past FP64_ZOOM raises
+        ValueError."""
         import torch
+        if any(needs_fp64(f["window"]) for f in frames):
+            raise ValueError("graph_batch: frames zoomed past FP64_ZOOM need render64")
         arr = self._frames(frames)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()

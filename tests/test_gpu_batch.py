@@ -103,3 +103,22 @@ def test_batch_argument_errors(ctx, asklib):
     with pytest.raises(asklib.AskError):
         ctx.render_batch([])
     torch.cuda.synchronize()
+
+
+def test_batch_routes_deep_frames_to_double(ctx, orc, asklib):
+    """Frames zoomed past 1e4 in a batch are rendered in binary64 after the
+    single-precision launch chain: every map equals the reference in its
+    precision, and the stats count the routed frames.  graph_batch refuses
+    them."""
+    deep = [(inputs.deep_window(nm)[0], 300 + 37 * k, 700, 4, 2, 8)
+            for k, (nm, *_) in enumerate(inputs.DEEP_SPOTS)]
+    specs = MIXED[:3] + deep[:2] + MIXED[3:5] + deep[2:]
+    frames = _frames(asklib, specs)
+    st = ctx.render_batch(frames, stats=True)
+    assert st["fp64_frames"] == 3
+    for (win, n, M, g, r, B), f in zip(specs, frames):
+        fp64 = asklib.needs_fp64(win)
+        want, _ = orc.render_ms(win, n, M, g, r, B, fp64=fp64)
+        assert np.array_equal(_map(f["out"]), want), (n, fp64)
+    with pytest.raises(ValueError):
+        ctx.graph_batch(frames)
