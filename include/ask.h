@@ -27,7 +27,8 @@
  * dx = (re_max - re_min) / n and dy = (im_max - im_min) / n in float.
  *
  * ask_render64 renders the exhaustive and ASK maps with the same sequence in
- * double precision, for deep zooms.
+ * double precision, for deep zooms, or in float-float arithmetic
+ * (ASK_FLAG_FLOAT_FLOAT).
  *
  * Output layout: uint32 dwell[py * n + px], row-major, py = 0 <-> im_min.
  *
