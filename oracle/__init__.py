@@ -13,7 +13,8 @@ zooms); this module only marshals numpy buffers.  Functions:
 * :func:`render_ms` -- serial recursive Mariani-Silver (Sec. 4.2.1, Sec. 6),
   with per-level statistics and an optional log of every region visited;
 * :func:`render_ms_region` -- one initial region of the g x g grid, for
-  sampled parity checks on maps too large to render on the CPU;
+  sampled parity checks on maps too large to render on the CPU (``fp64``:
+  double window, binary64 or float-float);
 * :func:`dwell64`, :func:`pixel_to_c64`, :func:`render_exhaustive64`,
   :func:`render_ms64` -- the same in double precision (deep zooms), the
   window given in double; with the flag ``FLOAT_FLOAT`` the maps iterate in
@@ -127,6 +128,10 @@ class Oracle:
         L.oracle_render_ms_region.argtypes = [P(Window), u32, u32, u32, u32, u32, u32,
                                               u32, u32, ctypes.c_void_p, ctypes.c_size_t,
                                               P(MSStats)]
+        L.oracle_render_ms_region64.argtypes = [P(Window64), u32, u32, u32, u32, u32, u32,
+                                              u32, u32, ctypes.c_void_p, ctypes.c_size_t,
+                                              P(MSStats)]
+        L.oracle_render_ms_region64.restype = ctypes.c_int
         self.lib = L
         self.path = path
 
@@ -205,7 +210,7 @@ class Oracle:
                                             ctypes.byref(w), ctypes.byref(h))
         return (x0.value, y0.value, w.value, h.value) if ok else None
 
-    def render_ms_region(self, window, n, max_dwell, g, r, B, gx, gy, flags=0):
+    def render_ms_region(self, window, n, max_dwell, g, r, B, gx, gy, flags=0, fp64=False):
         """Mariani-Silver tile of initial region (gx, gy).
 
         Returns ((x0, y0, w, h), tile[h, w], stats dict), or None for an
@@ -217,9 +222,10 @@ class Oracle:
         x0, y0, w_, h_ = reg
         tile = np.empty((h_, w_), dtype=np.uint32)
         st = MSStats()
-        w = _win(window)
-        rc = self.lib.oracle_render_ms_region(ctypes.byref(w), n, max_dwell, g, r, B, flags,
-                                              gx, gy, tile.ctypes.data, w_, ctypes.byref(st))
+        w = _win64(window) if fp64 else _win(window)
+        fn = self.lib.oracle_render_ms_region64 if fp64 else self.lib.oracle_render_ms_region
+        rc = fn(ctypes.byref(w), n, max_dwell, g, r, B, flags, gx, gy, tile.ctypes.data, w_,
+                ctypes.byref(st))
         if rc != 0:
             raise ValueError("oracle_render_ms_region failed (rc=%d)" % rc)
         return reg, tile, st.as_dict()

@@ -595,6 +595,12 @@ int oracle_initial_region(uint32_t n, uint32_t g, uint32_t gx, uint32_t gy,
     return initial_region(n, g, gx, gy, x0, y0, w, h, &s);
 }
 
+static int render_ms_region(const any_window *win, uint32_t n,
+                            uint32_t max_dwell, uint32_t g, uint32_t r,
+                            uint32_t B, uint32_t flags, uint32_t gx,
+                            uint32_t gy, uint32_t *tile, size_t tile_stride,
+                            oracle_ms_stats *stats);
+
 int oracle_render_ms_region(const oracle_window *win, uint32_t n,
                             uint32_t max_dwell, uint32_t g, uint32_t r,
                             uint32_t B, uint32_t flags, uint32_t gx,
@@ -602,6 +608,26 @@ int oracle_render_ms_region(const oracle_window *win, uint32_t n,
                             oracle_ms_stats *stats)
 {
     any_window aw = {win, NULL};
+    return render_ms_region(&aw, n, max_dwell, g, r, B, flags, gx, gy, tile, tile_stride, stats);
+}
+
+int oracle_render_ms_region64(const oracle_window64 *win, uint32_t n,
+                              uint32_t max_dwell, uint32_t g, uint32_t r,
+                              uint32_t B, uint32_t flags, uint32_t gx,
+                              uint32_t gy, uint32_t *tile, size_t tile_stride,
+                              oracle_ms_stats *stats)
+{
+    any_window aw = {NULL, win};
+    return render_ms_region(&aw, n, max_dwell, g, r, B, flags, gx, gy, tile, tile_stride, stats);
+}
+
+static int render_ms_region(const any_window *win, uint32_t n,
+                            uint32_t max_dwell, uint32_t g, uint32_t r,
+                            uint32_t B, uint32_t flags, uint32_t gx,
+                            uint32_t gy, uint32_t *tile, size_t tile_stride,
+                            oracle_ms_stats *stats)
+{
+    const any_window aw = *win;
     if (!tile || !ms_args_ok(&aw, n, max_dwell, g, r, B) || gx >= g || gy >= g)
         return -1;
     ms_job j;

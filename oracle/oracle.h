@@ -90,6 +90,13 @@ int oracle_render_ms_region(const oracle_window *win, uint32_t n,
                             uint32_t B, uint32_t flags, uint32_t gx,
                             uint32_t gy, uint32_t *tile, size_t tile_stride,
                             oracle_ms_stats *stats);
+/* The same for a double-precision window (binary64, or float-float with
+ * ORACLE_FLOAT_FLOAT in flags). */
+int oracle_render_ms_region64(const oracle_window64 *win, uint32_t n,
+                              uint32_t max_dwell, uint32_t g, uint32_t r,
+                              uint32_t B, uint32_t flags, uint32_t gx,
+                              uint32_t gy, uint32_t *tile, size_t tile_stride,
+                              oracle_ms_stats *stats);
 
 #ifdef __cplusplus
 }

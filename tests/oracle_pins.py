@@ -404,6 +404,22 @@ def pin_ff_tracks_double(orc):
         assert min(len(np.unique(ff[y])) for y in range(0, n, 7)) > 4
 
 
+def pin_regions_alone64(orc):
+    """One initial region rendered alone equals its tile of the full map, in
+    binary64 and in float-float."""
+    win = ANTENNA_WINDOW
+    for flags in (0, FLOAT_FLOAT):
+        full, st = orc.render_ms(win, 150, 600, 4, 3, 4, flags=flags, threads=2, fp64=True)
+        it = 0
+        for gy in range(4):
+            for gx in range(4):
+                (x0, y0, w, h), tile, rst = orc.render_ms_region(win, 150, 600, 4, 3, 4, gx, gy,
+                                                                 flags=flags, fp64=True)
+                assert np.array_equal(tile, full[y0:y0 + h, x0:x0 + w]), (flags, gx, gy)
+                it += rst["iterations"]
+        assert it == st["iterations"]
+
+
 def pin_ms_ff_invariants(orc):
     """The recursion's invariants on float-float maps; with fills off it
     equals the float-float exhaustive map."""
@@ -420,4 +436,5 @@ ALL_PINS = [pin_closed_forms, pin_exact_points, pin_exact_tiny_maps,
             pin_tree_by_hand, pin_ms_invariants, pin_uniform_windows, pin_stopping_side,
             pin_threads_and_regions, pin_closed_forms64, pin_exact_points64,
             pin_exact_tiny_maps64, pin_deep_zoom64, pin_ms64_invariants, pin_closed_forms_ff,
-            pin_exact_points_ff, pin_ff_tracks_double, pin_ms_ff_invariants]
+            pin_exact_points_ff, pin_ff_tracks_double, pin_ms_ff_invariants,
+            pin_regions_alone64]

@@ -199,3 +199,28 @@ def test_render64_invalid_arguments(ctx, asklib):
         assert e.value.status == asklib.EINVAL, (method, w, md)
     torch.cuda.synchronize()
     assert bool((out == 7).all())
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", PRECISIONS, ids=PREC_IDS)
+def test_deep_bench_size_sampled(ctx, orc, asklib, prec):
+    """The deep bench's workload at full size (n = 8192, seahorse valley
+    2^-30 wide, dwell cap 4096, g=128 r=4 B=16): 24 seeded initial regions
+    of the ASK map against the reference rendering each region alone, and
+    600 seeded pixels of the exhaustive map against the reference dwell of
+    the pixel's c."""
+    import oracle
+    name, flag, oflag = prec
+    win, M = inputs.deep_window("seahorse_2^-30")
+    n, g, r, B = 8192, 128, 4, 16
+    out = ctx.render64("ask", win, n, M, params(asklib, g, r, B, flags=flag))
+    got = host(out)
+    for gx, gy in inputs.sample_initial_regions(g, 24, seed=8192):
+        (x0, y0, w, h), tile, _ = orc.render_ms_region(win, n, M, g, r, B, gx, gy,
+                                                       flags=oflag, fp64=True)
+        assert first_diff(got[y0:y0 + h, x0:x0 + w], tile) is None, (name, gx, gy)
+    ex = host(ctx.render64("exhaustive", win, n, M, params(asklib, 1, 2, 1, flags=flag)))
+    for px, py in inputs.sample_pixels(n, 600, seed=8193):
+        cr, ci = orc.pixel_to_c64(win, n, px, py)
+        want = oracle.dwell_ff(cr, ci, M) if oflag else oracle.dwell64(cr, ci, M)
+        assert ex[py, px] == want, (name, px, py)
