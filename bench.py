@@ -804,7 +804,7 @@ def run_deep(args):
     # than in single precision
     def tune(flags):
         cands = [(args.g, args.r, args.B)] if args.no_tune else \
-            [(g, r, B) for g in (32, 64, 128) for r in (2, 4) for B in (8, 16, 32)]
+            [(g, r, B) for g in (32, 64, 128, 256) for r in (2, 4) for B in (8, 16, 32)]
         best = None
         for g, r, B in cands:
             p = ask.make_params(g, r, B, flags=flags)
