@@ -246,7 +246,10 @@ FP64_ZOOM = 1e4
 
 
 def needs_fp64(window):
-    """True for a window zoomed past FP64_ZOOM (narrower than 2 / FP64_ZOOM)."""
+    """True for a window (a 4-sequence, Window or Window64) zoomed past
+    FP64_ZOOM, i.e. narrower than 2 / FP64_ZOOM."""
+    if isinstance(window, (Window, Window64)):
+        window = (window.re_min, window.re_max, window.im_min, window.im_max)
     re0, re1, im0, im1 = (float(v) for v in window)
     return max(re1 - re0, im1 - im0) < 2.0 / FP64_ZOOM
 

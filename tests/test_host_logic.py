@@ -10,6 +10,9 @@ def test_fp64_threshold_is_zoom_1e4():
         assert ask.needs_fp64((-0.5 - hw, -0.5 + hw, 0.1 - hw, 0.1 + hw)) is want, zoom
     # the wider side decides: a window narrow in one direction only stays in float
     assert not ask.needs_fp64((0.0, 1.0, 0.0, 1e-6))
+    # the binding's window structures are accepted too
+    assert not ask.needs_fp64(ask.Window(-1.5, 0.5, -1.0, 1.0))
+    assert ask.needs_fp64(ask.Window64(0.3, 0.3 + 2.0 ** -30, 0.1, 0.1 + 2.0 ** -30))
 
 
 def test_batch_and_serving_workloads_stay_in_single_precision():
