@@ -263,7 +263,11 @@ def _window(w):
 
 
 def _window64(w):
-    return w if isinstance(w, Window64) else Window64(*[float(v) for v in w])
+    if isinstance(w, Window64):
+        return w
+    if isinstance(w, Window):
+        return Window64(w.re_min, w.re_max, w.im_min, w.im_max)
+    return Window64(*[float(v) for v in w])
 
 
 class Context:

@@ -32,3 +32,10 @@ def test_deep_inputs():
     assert a == inputs.deep_frames(8, 3)            # seeded
     assert all(ask.needs_fp64(f["window"]) for f in a)
     assert all(256 <= f["n"] <= 2048 and 512 <= f["max_dwell"] <= 4096 for f in a)
+
+
+def test_window64_conversion():
+    w = ask._window64(ask.Window(-1.5, 0.5, -1.0, 1.0))
+    assert (w.re_min, w.re_max, w.im_min, w.im_max) == (-1.5, 0.5, -1.0, 1.0)
+    w = ask._window64((0.1, 0.1 + 2.0 ** -40, 0.2, 0.2 + 2.0 ** -40))
+    assert w.re_max - w.re_min == 2.0 ** -40      # kept in double
