@@ -54,9 +54,20 @@ def recorded_traffic(kernel_key, workload):
         return None
 
 
-# z <- z^2 + c with the library's rounding: fma(-zi, zi, cr), fma(zr, zr, .),
-# zr + zr, fma(., zi, ci); the |z|^2 test is amortised over a block of updates
-FP32_OPS_PER_ITER = 4
+# FP32-pipe instructions per dwell iteration of the stepwise loop: zi*zi,
+# fma(zr, zr, zi2) for the test, fma(-zi, zi, cr), fma(zr, zr, t), zr + zr,
+# fma(., zi, ci): 1 FMUL + 4 FFMA + 1 FADD.  This is the roofline's unit.
+FP32_OPS_PER_ITER = 6
+# The kernels run updates in blocks with one test per block (escape is
+# absorbing), so an update that counts costs 3 FFMA + 1 FADD: the bound on
+# useful issue, reported beside the first.
+FP32_OPS_PER_UPDATE = 4
+# The headline's subdivision parameters (the 75-point sweep's pick on GB300;
+# the sweep still runs and its pick is reported).  The reference arm renders
+# the same map with the same parameters.
+HEADLINE_G, HEADLINE_R, HEADLINE_B = 16, 4, 16
+# The same for the n = 65536, dwell 4096 map (its sweep's pick on GB300).
+LARGE_G, LARGE_R, LARGE_B = 32, 2, 16
 
 
 def parse():
@@ -66,9 +77,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ask", choices=["ask", "reference"])
     ap.add_argument("--no-tune", action="store_true", help="skip the autotune sweep")
-    ap.add_argument("--g", type=int, default=32)
-    ap.add_argument("--r", type=int, default=4)
-    ap.add_argument("--B", type=int, default=16)
+    ap.add_argument("--tune-headline", action="store_true",
+                    help="time the headline at the sweep's pick instead of --g/--r/--B")
+    ap.add_argument("--g", type=int, default=HEADLINE_G)
+    ap.add_argument("--r", type=int, default=HEADLINE_R)
+    ap.add_argument("--B", type=int, default=HEADLINE_B)
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: skip the n=65536, batch and serving sub-results")
     ap.add_argument("--block", default="16x16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -226,13 +241,73 @@ def cpu_reference_sample(C, g, r, B, seconds, seed=2206, threads=None):
     return done_px, time.perf_counter() - t0, cores, used
 
 
+def workload_config(C, g, r, B, block):
+    """The `config` object of both arms: the workload and the subdivision
+    parameters that fix its map (the block shape does not change the map)."""
+    px = float(C["n"]) * C["n"]
+    return {"workload": C["name"], "n": C["n"], "max_dwell": C["max_dwell"],
+            "window": list(C["window"]), "g": g, "r": r, "B": B, "block": list(block),
+            "l2": "output map %.2f GB > 129 MB L2, rewritten every step" % (px * 4 / 1e9)}
+
+
+def measure_large(ctx, dev, local, world, steps=3, warmup=2):
+    """The n = 65536, dwell 4096 map (17.2 GB) rendered by ASK at its tuned
+    (g, r, B): `steps` timed renders with CUDA events, per-kernel times from
+    the timing ring, executed iterations from a counting render."""
+    import torch
+
+    from paper_2206_02255_gb300 import ask, inputs
+
+    C = inputs.C2
+    win, n, M = C["window"], C["n"], C["max_dwell"]
+    g, r, B = LARGE_G, LARGE_R, LARGE_B
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((n, n), dtype=torch.int32, device=dev)
+    p = ask.make_params(g, r, B)
+    _, cst = ctx.render("ask", win, n, M, ask.make_params(g, r, B, flags=ask.FLAG_COUNT), out=out,
+                        stats=True)
+    for _ in range(warmup):
+        ctx.render("ask", win, n, M, p, out=out)
+    ctx.timing_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    pt = ask.make_params(g, r, B, flags=ask.FLAG_TIMING)
+    ev[0].record(stream)
+    for k in range(steps):
+        ctx.render("ask", win, n, M, pt, out=out)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, ev[0].elapsed_time(ev[-1]) / steps, dev)
+    per = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
+    t = ctx.timing_read()
+    R = max(1, t["renders"])
+    del out
+    torch.cuda.empty_cache()
+    px = float(n) * n
+    return {"workload": C["name"], "n": n, "max_dwell": M, "window": list(win),
+            "g": g, "r": r, "B": B, "steps": steps, "ms_per_step": ms,
+            "gpix_s": world * px / (ms / 1e3) / 1e9, "min_ms": per[0], "max_ms": per[-1],
+            "dwell_iter_s_executed": cst["iterations"] / (ms / 1e3),
+            "kernels_ms": {"leaf": t["ms_leaf"] / R,
+                           "levels": [x / R for x in t["ms_per_level"][:cst["levels"]]]},
+            "leaf_iterations": cst["leaf_iterations"], "levels": cst["levels"],
+            "leaves": cst["leaves"], "gpu_launches_per_step": cst["kernel_launches"],
+            "l2": "output map %.1f GB > 129 MB L2" % (4 * px / 1e9), "clocks": clk}
+
+
 def run_reference(args):
     from paper_2206_02255_gb300 import inputs
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return
     C = inputs.C1
-    g, r, B = 32, 4, 16
+    g, r, B = args.g, args.r, args.B
+    block = tuple(int(v) for v in args.block.split("x"))
     per_step = 4.0
     for _ in range(args.warmup):
         cpu_reference_sample(C, g, r, B, 0.5)
@@ -250,8 +325,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": C["name"], "n": C["n"], "max_dwell": C["max_dwell"],
-                       "window": list(C["window"]), "g": g, "r": r, "B": B},
+            "config": workload_config(C, g, r, B, block), "method": "oracle (CPU, all host cores)",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -298,9 +372,14 @@ def run_gpu(args):
         return e0.elapsed_time(e1) / reps
 
     # ---- untimed autotune: (g, r, B) sweep, then block shape -------------
+    # The headline runs at --g/--r/--B (the sweep's usual pick, shared with
+    # the reference arm) unless --tune-headline; the sweep's pick is reported.
     tune = {"g": args.g, "r": args.r, "B": args.B, "block": [bx, by]}
+    if large and (args.g, args.r, args.B) == (HEADLINE_G, HEADLINE_R, HEADLINE_B):
+        tune.update(g=LARGE_G, r=LARGE_R, B=LARGE_B)
     sweep = []
-    if not args.no_tune:
+    swept = None
+    if not args.no_tune and (not large or args.tune_headline):
         best = None
         for g, r, B in inputs.c1_sweep():
             ms = time_renders("ask", g, r, B, (16, 16), 2)
@@ -313,7 +392,11 @@ def run_gpu(args):
             ms = time_renders("ask", g, r, B, blk, 3)
             if bbest is None or ms < bbest[1]:
                 bbest = (blk, ms)
-        tune = {"g": g, "r": r, "B": B, "block": list(bbest[0])}
+        swept = {"g": g, "r": r, "B": B, "block": list(bbest[0]), "ms": bbest[1],
+                 "headline_ms_same_reps": time_renders("ask", tune["g"], tune["r"], tune["B"],
+                                                       (bx, by), 3)}
+        if args.tune_headline:
+            tune = {k: swept[k] for k in ("g", "r", "B", "block")}
     g, r, B, blk = tune["g"], tune["r"], tune["B"], tuple(tune["block"])
 
     # ---- counting run (untimed): algorithmic work per kernel ---------------
@@ -436,14 +519,27 @@ def run_gpu(args):
         f_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         pass
-    # one dwell iteration needs at least 3 FFMA + 1 FADD on the FP32 pipe
+    # The roofline's unit is the stepwise iteration's 6 FP32-pipe instructions
+    # (1 FMUL + 4 FFMA + 1 FADD); "frac_useful_4op" takes the 4 instructions
+    # an update costs when the test is amortised over a block (3 FFMA +
+    # 1 FADD), the bound on useful issue.  achieved = the dominant kernel's
+    # dwell iterations (a counting render) / its mean CUDA-event time.
     peak = sms * 128 * f_mhz * 1e6 / FP32_OPS_PER_ITER / 1e9
+    peak4 = sms * 128 * f_mhz * 1e6 / FP32_OPS_PER_UPDATE / 1e9
     key = "leaf_refill_kernel" if dom == "leaf" else "level_kernel_" + dom
     traffic = recorded_traffic(key, C["name"]) if (g, r, B) == (16, 4, 16) else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "Gdwell-iter/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / %d FP32 ops per iteration"
-                              % (sms, f_mhz, FP32_OPS_PER_ITER)}
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz) / %d FP32-pipe "
+                              "instructions per stepwise iteration" % (sms, f_mhz, FP32_OPS_PER_ITER),
+                "frac_useful_4op": achieved / peak4,
+                "peak_useful_4op": peak4,
+                "peak_useful_4op_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / %d FP32-pipe "
+                                         "instructions per blocked update (3 FFMA + 1 FADD)"
+                                         % (sms, f_mhz, FP32_OPS_PER_UPDATE),
+                "achieved_basis": "%d dwell iterations of the %s kernel (counting render) / "
+                                  "%.4f ms mean CUDA-event time over %d timed steps"
+                                  % (it_dom, dom, kern[dom], R)}
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (
             sms * 128 * clk["sm_mhz"] * 1e6 / FP32_OPS_PER_ITER / 1e9)
@@ -474,21 +570,36 @@ def run_gpu(args):
                          "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     # ---- end to end through the C ABI with a host buffer -------------------
+    # ask_render_host takes the window and parameters by value and writes
+    # the map into a pinned host buffer: the call has no input array, so
+    # nothing is copied host -> device.  Between calls a plain device ->
+    # host copy of the same 1 GiB (no render) probes the host link, so a
+    # slow call can be told apart from a slow link.
     e2e = None
     if not args.no_e2e:
         host = torch.empty((n, n), dtype=torch.int32, pin_memory=True)
         for _ in range(3):  # warm-up calls (the host buffer's pages, the band events)
             ctx.render_host("ask", win, n, M, ask.make_params(g, r, B, blk), out=host)
         k_e2e = max(3, args.steps // 2)
+
+        def link_probe():
+            torch.cuda.synchronize(dev)
+            tc = time.perf_counter()
+            host.copy_(out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            return 1e3 * (time.perf_counter() - tc)
+
         barrier(world)
         calls = []
-        t0 = time.perf_counter()
+        t_calls = 0.0
         for _ in range(k_e2e):
             tc = time.perf_counter()
             ctx.render_host("ask", win, n, M, ask.make_params(g, r, B, blk), out=host)
-            calls.append(1e3 * (time.perf_counter() - tc))
-        t_e2e = (time.perf_counter() - t0) / k_e2e
-        t_e2e = max_over_ranks(world, t_e2e, dev)
+            dt = time.perf_counter() - tc
+            t_calls += dt
+            calls.append(1e3 * dt)
+        t_e2e = max_over_ranks(world, t_calls / k_e2e, dev)
+        probes = [link_probe() for _ in range(k_e2e)]
         # the same call with the map rendered in device memory and copied after
         staged = ask.make_params(g, r, B, blk, ask.FLAG_STAGED_COPY)
         ctx.render_host("ask", win, n, M, staged, out=host)
@@ -496,10 +607,16 @@ def run_gpu(args):
         for _ in range(k_e2e):
             ctx.render_host("ask", win, n, M, staged, out=host)
         t_staged = max_over_ranks(world, (time.perf_counter() - t0) / k_e2e, dev)
+        sc, sp = sorted(calls), sorted(probes)
         e2e = {"value": world * pixels / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": int(pixels * 4), "ms_per_step": 1e3 * t_e2e,
+               "inputs": "none: window, n, max_dwell and (g, r, B) are passed by value",
                "path": "banded: each band of initial-region rows is copied while the next renders",
-               "ms_per_call": calls, "staged_copy_ms_per_step": 1e3 * t_staged}
+               "ms_per_call": calls, "p50_ms": percentile(sc, 50), "p99_ms": percentile(sc, 99),
+               "value_at_p50": world * pixels / (percentile(sc, 50) / 1e3) / 1e9,
+               "link_probe_ms": probes,
+               "link_probe_gbs_p50": 4 * pixels / (percentile(sp, 50) / 1e3) / 1e9,
+               "staged_copy_ms_per_step": 1e3 * t_staged}
         del host
 
     # ---- CPU reference on a bounded sample (rank 0, N = 1) -----------------
@@ -513,16 +630,27 @@ def run_gpu(args):
                "single_thread": {"value": px1 / t1 / 1e9, "cores": 1,
                                  "sample": "%d seeded initial regions (%d pixels)" % (regions1, px1)}}
 
+    # ---- the other configurations as compact sub-results of the same run:
+    #      n = 65536 map, 256-frame batch, served requests
+    subs = {}
+    if args.workload == "single" and not args.headline_only and args.n is None \
+            and args.max_dwell is None:
+        del out
+        torch.cuda.empty_cache()
+        subs["large"] = measure_large(ctx, dev, local, world)
+        subs["batch"] = measure_batch(ctx, dev, local, world, rank, 256, steps=1, warmup=1,
+                                      probes=4, full=False)
+        subs["serve"] = measure_serve(ctx, dev, local, world, rank, sat_passes=1)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": C["name"], "n": n, "max_dwell": M, "window": list(win),
-                       "method": "ask", "g": g, "r": r, "B": B, "block": list(blk),
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "output map %.2f GB > 129 MB L2, rewritten every step" % (pixels * 4 / 1e9)},
+            "config": workload_config(C, g, r, B, blk),
+            "method": "ask", "parallelism": "replicas" if world > 1 else "single",
+            "tune": swept,
             "dwell_iter_s": {"executed": cst["iterations"] / (ms_step / 1e3),
                              "exhaustive_equivalent": est["iterations"] / (ms_step / 1e3)},
             "step_ms": step_pct,
@@ -548,6 +676,7 @@ def run_gpu(args):
             "clocks": clk,
             "tune_sweep_top5": sorted(sweep, key=lambda t: t[3])[:5],
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -558,18 +687,17 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 # Batched workload: 256 frames, sides 512..8192, zoomed on boundary points
 # ---------------------------------------------------------------------------
-def run_batch(args):
+def measure_batch(ctx, dev, local, world, rank, nframes, steps, warmup, probes=6, full=True):
+    """The batched workload: per-frame ASK against one batch (and its CUDA
+    graph).  Returns the measured quantities as a dict; `full` adds the
+    model-vs-measured comparison of the tuner's probes and the end-to-end
+    pass."""
     import torch
 
-    from paper_2206_02255_gb300 import ask, autotune, build, costmodel, inputs
+    from paper_2206_02255_gb300 import ask, autotune, inputs
 
-    world, rank, local = dist_init()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    ctx = ask.Context(local)
     stream = torch.cuda.current_stream(dev)
-    frames = inputs.batch_frames(count=args.frames, seed=0 + rank)
+    frames = inputs.batch_frames(count=nframes, seed=0 + rank)
     sizes = [f["n"] * f["n"] for f in frames]
     pad = [(z + 3) // 4 * 4 for z in sizes]               # keep every map 16-byte aligned
     total_px = float(sum(sizes))
@@ -579,25 +707,27 @@ def run_batch(args):
         f["out"] = big[off:off + z].view(f["n"], f["n"])
         off += zp
 
-    tuner = autotune.BatchTuner(ctx, probes=6).fit(frames)
+    tuner = autotune.BatchTuner(ctx, probes=probes).fit(frames)
     for f in frames:
         f["g"], f["r"], f["B"] = tuner.choose(f)
     probe_models = []
-    for pf, cfg, _ in tuner.probes:
-        mc = autotune.model_choice(ctx, pf["window"], pf["n"], pf["max_dwell"], cfg["g"], cfg["r"],
-                                   cfg["B"])
-        try:
-            scratch = torch.empty((pf["n"], pf["n"]), dtype=torch.int32, device=dev)
-            model_ms = autotune.time_config(ctx, pf["window"], pf["n"], pf["max_dwell"], mc["g"],
-                                            mc["r"], mc["B"], scratch)
-            del scratch
-        except ask.AskError:
-            model_ms = None
-        probe_models.append(dict(n=pf["n"], max_dwell=pf["max_dwell"],
-                                 measured=(cfg["g"], cfg["r"], cfg["B"]), measured_ms=round(cfg["ms"], 3),
-                                 model=(mc["g"], mc["r"], mc["B"]),
-                                 model_ms=None if model_ms is None else round(model_ms, 3),
-                                 P=round(mc["P"], 3), lambda_fit=round(mc["lam"], 2)))
+    if full:
+        for pf, cfg, _ in tuner.probes:
+            mc = autotune.model_choice(ctx, pf["window"], pf["n"], pf["max_dwell"], cfg["g"],
+                                       cfg["r"], cfg["B"])
+            try:
+                scratch = torch.empty((pf["n"], pf["n"]), dtype=torch.int32, device=dev)
+                model_ms = autotune.time_config(ctx, pf["window"], pf["n"], pf["max_dwell"], mc["g"],
+                                                mc["r"], mc["B"], scratch)
+                del scratch
+            except ask.AskError:
+                model_ms = None
+            probe_models.append(dict(n=pf["n"], max_dwell=pf["max_dwell"],
+                                     measured=(cfg["g"], cfg["r"], cfg["B"]),
+                                     measured_ms=round(cfg["ms"], 3),
+                                     model=(mc["g"], mc["r"], mc["B"]),
+                                     model_ms=None if model_ms is None else round(model_ms, 3),
+                                     P=round(mc["P"], 3), lambda_fit=round(mc["lam"], 2)))
 
     def per_frame():
         for f in frames:
@@ -609,64 +739,88 @@ def run_batch(args):
 
     graph = ctx.graph_batch(frames)
 
-    def timed(fn, steps):
-        for _ in range(max(1, args.warmup)):
+    def timed(fn, k):
+        for _ in range(max(1, warmup)):
             fn()
         barrier(world)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(k):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        return max_over_ranks(world, e0.elapsed_time(e1) / steps, dev)
+        return max_over_ranks(world, e0.elapsed_time(e1) / k, dev)
 
     clocks = ClockSampler(local)
-    ms_frame = timed(per_frame, args.steps)
+    ms_frame = timed(per_frame, steps)
     clocks.start()
     time.sleep(0.3)
-    ms_batch = timed(batched, args.steps)
+    ms_batch = timed(batched, steps)
     clk = clocks.stop()
-    ms_graph = timed(graph.launch, args.steps)
-    _, st = None, ctx.render_batch(frames, flags=ask.FLAG_COUNT, stats=True)
+    ms_graph = timed(graph.launch, steps)
+    st = ctx.render_batch(frames, flags=ask.FLAG_COUNT, stats=True)
     launches = st["kernel_launches"]
-
-    # end to end: the batched render plus every map copied to pinned host memory
-    host = torch.empty(sum(pad), dtype=torch.int32, pin_memory=True)
-    steps_e2e = max(2, args.steps // 2)
-    batched()
-    host.copy_(big, non_blocking=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(steps_e2e):
+    graph.close()
+    gp = lambda ms: world * total_px / (ms / 1e3) / 1e9
+    res = {"frames": len(frames), "pixels": int(total_px),
+           "per_frame_ask": {"ms": ms_frame, "gpix_s": gp(ms_frame)},
+           "batched": {"ms": ms_batch, "gpix_s": gp(ms_batch), "launches": launches},
+           "graph": {"ms": ms_graph, "gpix_s": gp(ms_graph)},
+           "speedup_batch_vs_per_frame": ms_frame / ms_batch,
+           "dwell_iter_s": {"executed": st["iterations"] / (ms_batch / 1e3)},
+           "tuned_probes": tuner.summary(), "clocks": clk, "steps": steps}
+    if full:
+        res["model_vs_measured"] = probe_models
+        # end to end: the batched render plus every map copied to pinned host memory
+        host = torch.empty(sum(pad), dtype=torch.int32, pin_memory=True)
+        steps_e2e = max(2, steps // 2)
         batched()
         host.copy_(big, non_blocking=True)
         torch.cuda.synchronize(dev)
-    t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / steps_e2e, dev)
-    graph.close()
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            batched()
+            host.copy_(big, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / steps_e2e, dev)
+        res["e2e"] = {"value": gp(t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": int(4 * total_px), "ms_per_step": 1e3 * t_e2e}
+        del host
+    for f in frames:
+        f["out"] = None
+    del big
+    torch.cuda.empty_cache()
+    return res
 
+
+def run_batch(args):
+    import torch
+
+    from paper_2206_02255_gb300 import ask, build
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    ctx = ask.Context(local)
+    res = measure_batch(ctx, dev, local, world, rank, args.frames, args.steps, args.warmup)
     if rank == 0:
-        gp = lambda ms: world * total_px / (ms / 1e3) / 1e9
+        b = res["batched"]
         line = {
-            "metric": METRIC, "value": gp(ms_batch), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "metric": METRIC, "value": b["gpix_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "batch_%d_frames_side512-8192_zoom1-1e4_dwell256-8192" % len(frames),
-                       "frames": len(frames), "pixels": int(total_px), "method": "ask_batch",
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "%.1f GB of maps per step > 129 MB L2" % (4 * total_px / 1e9)},
-            "per_frame_ask": {"ms": ms_frame, "gpix_s": gp(ms_frame)},
-            "batched": {"ms": ms_batch, "gpix_s": gp(ms_batch), "launches": launches},
-            "graph": {"ms": ms_graph, "gpix_s": gp(ms_graph)},
-            "speedup_batch_vs_per_frame": ms_frame / ms_batch,
-            "dwell_iter_s": {"executed": st["iterations"] / (ms_batch / 1e3)},
-            "tuned_probes": tuner.summary(), "model_vs_measured": probe_models,
-            "e2e": {"value": gp(t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": int(4 * total_px), "ms_per_step": 1e3 * t_e2e},
-            "gpu_launches": launches * args.steps, "clocks": clk,
+            "config": {"workload": "batch_%d_frames_side512-8192_zoom1-1e4_dwell256-8192"
+                                   % res["frames"],
+                       "frames": res["frames"], "pixels": res["pixels"],
+                       "l2": "%.1f GB of maps per step > 129 MB L2" % (4 * res["pixels"] / 1e9)},
+            "method": "ask_batch", "parallelism": "replicas" if world > 1 else "single",
+            "e2e": res.pop("e2e"), "gpu_launches": b["launches"] * args.steps,
+            "clocks": res.pop("clocks"),
         }
+        line.update(res)
         print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -674,17 +828,16 @@ def run_batch(args):
 # ---------------------------------------------------------------------------
 # Served workload: Poisson render requests, continuous batching
 # ---------------------------------------------------------------------------
-def run_serve(args):
+def measure_serve(ctx, dev, local, world, rank, sat_passes=3, count=2000):
+    """The served workload: Poisson requests (lambda = 200/s, seed 7) through
+    the continuous-batching server and through per-frame ASK, then the first
+    600 requests all waiting at t = 0 (saturation), `sat_passes` passes of
+    each, the median pass reported.  Returns a dict."""
     import torch
 
-    from paper_2206_02255_gb300 import ask, autotune, build, inputs, serve
+    from paper_2206_02255_gb300 import autotune, inputs, serve
 
-    world, rank, local = dist_init()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    ctx = ask.Context(local)
-    reqs = inputs.serving_requests(count=2000, seed=7 + rank)
+    reqs = inputs.serving_requests(count=count, seed=7 + rank)
     tuner = autotune.BatchTuner(ctx, probes=4).fit(reqs[::20])
     cfg = {d["id"]: tuner.choose(d) for d in reqs}
 
@@ -707,49 +860,70 @@ def run_serve(args):
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
+    s0, b0 = srv.single_dispatches, srv.batch_dispatches
     served = serve.summarize(srv.run(fresh(reqs)))
+    dispatches = {"single_frame": srv.single_dispatches - s0, "batches": srv.batch_dispatches - b0}
     clk = clocks.stop()
     alone = serve.summarize(serve.serve_per_frame(ctx, fresh(reqs), pool=pool, keep=False,
                                                   dpool=dpool))
-    # saturation: the first 600 requests all waiting at t = 0.  One untimed
-    # pass first fills the buffer pools to the depth full batches need (a
-    # server in steady state holds them; allocating on demand is slow).
-    # Three passes of each; the median pass is reported (the batches a
-    # saturated server forms depend on host timing, so passes differ).
+    # saturation: one untimed pass first fills the buffer pools to the depth
+    # full batches need (a server in steady state holds them)
     srv.run(fresh(reqs[:600], at_zero=True))
-    sat_s = sorted((serve.summarize(srv.run(fresh(reqs[:600], at_zero=True))) for _ in range(3)),
-                   key=lambda r: r["gpix_s"])
+    sat_s = sorted((serve.summarize(srv.run(fresh(reqs[:600], at_zero=True)))
+                    for _ in range(sat_passes)), key=lambda r: r["gpix_s"])
     sat_a = sorted((serve.summarize(serve.serve_per_frame(ctx, fresh(reqs[:600], at_zero=True),
                                                           pool=pool, keep=False, dpool=dpool))
-                    for _ in range(3)),
-                   key=lambda r: r["gpix_s"])
-    sat_served, sat_alone = sat_s[1], sat_a[1]
+                    for _ in range(sat_passes)), key=lambda r: r["gpix_s"])
+    sat_served, sat_alone = sat_s[len(sat_s) // 2], sat_a[len(sat_a) // 2]
     srv.close()
+    torch.cuda.empty_cache()
     px = float(sum(d["n"] * d["n"] for d in reqs))
-    value = whole_job_rate(world, px, served["span_s"], dev) / 1e9
+    return {"requests": len(reqs), "pixels": int(px), "rate_per_s": 200,
+            "span_s": served["span_s"],
+            "gpix_s": whole_job_rate(world, px, served["span_s"], dev) / 1e9,
+            "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"], "max": served["max_ms"]},
+            "dispatches": dispatches,
+            "per_frame_ask": {"p50_ms": alone["p50_ms"], "p99_ms": alone["p99_ms"],
+                              "max_ms": alone["max_ms"], "gpix_s": alone["gpix_s"]},
+            "saturated_600": {"served_gpix_s": sat_served["gpix_s"],
+                              "per_frame_gpix_s": sat_alone["gpix_s"],
+                              "served_p50_ms": sat_served["p50_ms"],
+                              "served_p99_ms": sat_served["p99_ms"],
+                              "per_frame_p50_ms": sat_alone["p50_ms"],
+                              "per_frame_p99_ms": sat_alone["p99_ms"],
+                              "passes": sat_passes, "reported": "median pass",
+                              "served_gpix_s_all": [r["gpix_s"] for r in sat_s],
+                              "per_frame_gpix_s_all": [r["gpix_s"] for r in sat_a]},
+            "clocks": clk}
+
+
+def run_serve(args):
+    import torch
+
+    from paper_2206_02255_gb300 import ask, build
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    ctx = ask.Context(local)
+    res = measure_serve(ctx, dev, local, world, rank)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * served["span_s"],
+            "metric": METRIC, "value": res["gpix_s"], "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * res["span_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "serve_2000_poisson200_side256-4096_dwell512-4096",
-                       "requests": len(reqs), "rate_per_s": 200, "budget_gb": 40, "slots": 2,
-                       "pixels": int(px), "method": "ask_batch continuous batching"},
-            "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"], "max": served["max_ms"]},
-            "per_frame_ask": {"p50_ms": alone["p50_ms"], "p99_ms": alone["p99_ms"],
-                              "gpix_s": alone["gpix_s"]},
-            "saturated_600": {"served_gpix_s": sat_served["gpix_s"],
-                              "per_frame_gpix_s": sat_alone["gpix_s"],
-                              "served_p99_ms": sat_served["p99_ms"],
-                              "per_frame_p99_ms": sat_alone["p99_ms"],
-                              "passes": 3, "reported": "median pass",
-                              "served_gpix_s_all": [r["gpix_s"] for r in sat_s],
-                              "per_frame_gpix_s_all": [r["gpix_s"] for r in sat_a]},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": int(4 * px), "note": "latency includes the D2H copy"},
-            "clocks": clk,
+                       "requests": res["requests"], "rate_per_s": 200, "budget_gb": 40, "slots": 2,
+                       "pixels": res["pixels"]},
+            "method": "ask continuous batching",
+            "e2e": {"value": res["gpix_s"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 4 * res["pixels"],
+                    "note": "latency includes the D2H copy"},
+            "clocks": res.pop("clocks"),
         }
+        line.update(res)
         print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -901,6 +1075,7 @@ def run_deep(args):
             "roofline": {"bound": "alu", "kernel": "leaf64_kernel", "achieved": leaf_gops,
                          "peak": FP64_PEAK_GOPS, "unit": "G FP64-pipe ops/s",
                          "frac": leaf_gops / FP64_PEAK_GOPS, "traffic": None,
+                         "of": "nominal (no measured FP64 peak on this GPU)",
                          "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2 flops); no measured "
                                         "FP64 peak",
                          "work": "leaf pixels' dwells x %d FP64 ops / mean leaf-kernel time" %

@@ -12,6 +12,12 @@ slot's copy stream while the next batch renders.  Requests that arrive
 while batches run wait for the next free slot.  A request's latency runs
 from its arrival to the moment its map is in host memory.
 
+Batching pays only when requests queue up.  A slot that admits a single
+request dispatches it through the single-frame call (no frame table to
+build and copy), so a lightly loaded server adds nothing to the per-frame
+path.  While work is in flight the server polls its events without
+sleeping; it sleeps only when it is idle until the next arrival.
+
 Requests zoomed past ``ask.FP64_ZOOM`` are rendered in double precision
 (``ask_render64``) on the same compute stream, after their batch's
 single-precision frames.
@@ -113,6 +119,8 @@ class Server:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]  # copies
         self.busy = [None] * slots       # list of requests in flight per slot
         self.used = 0                    # bytes of dwell buffers in flight
+        self.single_dispatches = 0       # slots that took one request alone
+        self.batch_dispatches = 0
 
     def close(self):
         for c in self.ctxs:
@@ -125,13 +133,19 @@ class Server:
             for q in reqs:
                 q.dbuf, q.out = self.dpool.get(q.n)
                 q.hbuf, q.host = self.pool.get(q.n)
-            frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r, B=q.B,
-                           out=q.out) for q in reqs if not ask.needs_fp64(q.window)]
-            if frames:
-                self.ctxs[slot].render_batch(frames, stream=c)
-            for q in reqs:
-                if ask.needs_fp64(q.window):
-                    render_one(self.ctxs[slot], q, c)
+            if len(reqs) == 1:
+                # nothing queued behind it: the single-frame call
+                render_one(self.ctxs[slot], reqs[0], c)
+                self.single_dispatches += 1
+            else:
+                frames = [dict(window=q.window, n=q.n, max_dwell=q.max_dwell, g=q.g, r=q.r,
+                               B=q.B, out=q.out) for q in reqs if not ask.needs_fp64(q.window)]
+                if frames:
+                    self.ctxs[slot].render_batch(frames, stream=c)
+                for q in reqs:
+                    if ask.needs_fp64(q.window):
+                        render_one(self.ctxs[slot], q, c)
+                self.batch_dispatches += 1
             rendered = torch.cuda.Event()
             rendered.record(c)
         s.wait_event(rendered)
@@ -144,9 +158,12 @@ class Server:
             q.event = ev
         self.busy[slot] = reqs
 
-    def run(self, requests, poll_s=0.0002):
+    def run(self, requests, idle_spin_s=0.0003):
         """Serve `requests` (sorted by arrival time t, seconds from start) in
-        real time; returns them with t_done set (seconds from start)."""
+        real time; returns them with t_done set (seconds from start).  While
+        batches are in flight the loop polls without sleeping; when nothing
+        is in flight and nothing waits, it sleeps until `idle_spin_s` before
+        the next arrival and spins from there."""
         pending = []
         k = 0
         t0 = time.perf_counter()
@@ -184,11 +201,9 @@ class Server:
                     self._start(slot, take)
             if k < len(requests) and not pending and all(b is None for b in self.busy):
                 # idle until the next arrival
-                wait = requests[k].t - (time.perf_counter() - t0)
+                wait = requests[k].t - (time.perf_counter() - t0) - idle_spin_s
                 if wait > 0:
                     time.sleep(min(wait, 0.01))
-            else:
-                time.sleep(poll_s)
         return requests
 
 
@@ -202,17 +217,22 @@ def render_one(ctx, q, stream):
         ctx.render("ask", q.window, q.n, q.max_dwell, p, out=q.out, stream=stream)
 
 
-def serve_per_frame(ctx, requests, poll_s=0.0002, pool=None, keep=True, dpool=None):
+def serve_per_frame(ctx, requests, idle_spin_s=0.0003, pool=None, keep=True, dpool=None):
     """Baseline: one request at a time in arrival order, single-frame ASK,
-    map copied to pinned host memory; returns requests with t_done set."""
+    map copied to pinned host memory; returns requests with t_done set.  It
+    waits for an arrival as the server does: asleep until `idle_spin_s`
+    before it, spinning from there."""
     import torch
     pool = pool if pool is not None else PinnedPool()
     dpool = dpool if dpool is not None else DevicePool(ctx.device)
     s = torch.cuda.Stream(device=ctx.device)
     t0 = time.perf_counter()
     for q in requests:
+        wait = q.t - (time.perf_counter() - t0) - idle_spin_s
+        if wait > 0:
+            time.sleep(wait)
         while time.perf_counter() - t0 < q.t:
-            time.sleep(poll_s)
+            pass
         with torch.cuda.stream(s):
             q.dbuf, q.out = dpool.get(q.n)
             q.hbuf, q.host = pool.get(q.n)
