@@ -737,7 +737,11 @@ def measure_batch(ctx, dev, local, world, rank, nframes, steps, warmup, probes=6
     def batched():
         ctx.render_batch(frames)
 
+    def persistent():
+        ctx.render_batch(frames, flags=ask.FLAG_PERSISTENT)
+
     graph = ctx.graph_batch(frames)
+    pgraph = ctx.graph_batch(frames, flags=ask.FLAG_PERSISTENT)
 
     def timed(fn, k):
         for _ in range(max(1, warmup)):
@@ -759,15 +763,30 @@ def measure_batch(ctx, dev, local, world, rank, nframes, steps, warmup, probes=6
     ms_batch = timed(batched, steps)
     clk = clocks.stop()
     ms_graph = timed(graph.launch, steps)
+    clocks_p = ClockSampler(local)
+    clocks_p.start()
+    time.sleep(0.3)
+    ms_pers = timed(persistent, steps)
+    clk_p = clocks_p.stop()
+    ms_pgraph = timed(pgraph.launch, steps)
     st = ctx.render_batch(frames, flags=ask.FLAG_COUNT, stats=True)
     launches = st["kernel_launches"]
+    stp = ctx.render_batch(frames, flags=ask.FLAG_COUNT | ask.FLAG_PERSISTENT, stats=True)
     graph.close()
+    pgraph.close()
     gp = lambda ms: world * total_px / (ms / 1e3) / 1e9
     res = {"frames": len(frames), "pixels": int(total_px),
            "per_frame_ask": {"ms": ms_frame, "gpix_s": gp(ms_frame)},
-           "batched": {"ms": ms_batch, "gpix_s": gp(ms_batch), "launches": launches},
+           "batched": {"ms": ms_batch, "gpix_s": gp(ms_batch), "launches": launches,
+                       "form": "launch chain: init, one level kernel per depth, leaf kernel"},
            "graph": {"ms": ms_graph, "gpix_s": gp(ms_graph)},
+           "persistent": {"ms": ms_pers, "gpix_s": gp(ms_pers), "launches": stp["kernel_launches"],
+                          "form": "init kernel + one persistent kernel over a device work queue",
+                          "clocks": clk_p},
+           "persistent_graph": {"ms": ms_pgraph, "gpix_s": gp(ms_pgraph)},
            "speedup_batch_vs_per_frame": ms_frame / ms_batch,
+           "speedup_persistent_vs_chain": ms_batch / ms_pers,
+           "speedup_persistent_vs_per_frame": ms_frame / ms_pers,
            "dwell_iter_s": {"executed": st["iterations"] / (ms_batch / 1e3)},
            "tuned_probes": tuner.summary(), "clocks": clk, "steps": steps}
     if full:

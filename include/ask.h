@@ -122,6 +122,25 @@ typedef enum {
 /* ask_render64 only: iterate in float-float arithmetic on the FP32 pipe
  * instead of binary64 (see ask_render64). */
 #define ASK_FLAG_FLOAT_FLOAT 1024u
+/* ask_render_batch / ask_graph_create_batch: render the batch with one
+ * persistent kernel fed from a device work queue (after an init kernel that
+ * writes every frame's initial regions), instead of one level kernel per
+ * subdivision depth.  The queue holds the regions of every frame and every
+ * depth, each region's perimeter query possibly cut into chunk items;
+ * deciding a region pushes its children (or fill bands) back onto the queue
+ * or appends it to a leaf list that the same kernel's warps work through
+ * whenever they have no region item ready, so depths and leaves overlap with
+ * no grid-wide step (Sec. 5's region tables kept on the device, without the
+ * per-depth launches).  Same maps.  Every device-side wait is bounded: a
+ * render in which no warp finds work for a long time (about a minute of
+ * back-off polls, counted afresh whenever the queue or the leaf list moves)
+ * latches a timeout, reported as ASK_ETIMEOUT by the next synchronising
+ * call.  Combines with ASK_FLAG_COUNT, not with ASK_FLAG_EXACT_BORDERS. */
+#define ASK_FLAG_PERSISTENT 2048u
+/* Tests of the timeout path only (with ASK_FLAG_PERSISTENT): a warp gives
+ * up at its first idle poll, so a render where some warp ever waits latches
+ * the timeout and returns ASK_ETIMEOUT; its map is incomplete. */
+#define ASK_FLAG_WAIT_TEST 4096u
 
 typedef struct {
     float re_min, re_max, im_min, im_max;
@@ -230,7 +249,10 @@ typedef struct {
  * level kernel per subdivision depth whose work queue holds the regions of
  * every frame at that depth, the deferred-fill kernel and one leaf kernel
  * over the leaves of every frame (ASK, Sec. 5, with region records that name
- * their frame).  flags: ASK_FLAG_COUNT, ASK_FLAG_EXACT_BORDERS.  Maps are
+ * their frame); with ASK_FLAG_PERSISTENT, one persistent kernel over a device
+ * work queue instead (see the flag).  flags: ASK_FLAG_COUNT,
+ * ASK_FLAG_EXACT_BORDERS (not with ASK_FLAG_PERSISTENT), ASK_FLAG_PERSISTENT,
+ * ASK_FLAG_WAIT_TEST.  Maps are
  * identical to rendering each frame alone with ask_render.  Asynchronous on
  * `stream` unless stats != NULL (then it synchronises and sums counts over
  * the frames).  The context's batch scratch grows as needed. */
@@ -239,8 +261,8 @@ ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nfra
 
 /* A batch render captured as a CUDA graph with its own scratch: replaying it
  * renders the same frames into the same buffers with one graph launch.
- * flags: ASK_FLAG_EXACT_BORDERS only.  Creation allocates and synchronises
- * `stream`; launches do neither. */
+ * flags: ASK_FLAG_EXACT_BORDERS or ASK_FLAG_PERSISTENT.  Creation allocates
+ * and synchronises `stream`; launches do neither. */
 typedef struct ask_graph ask_graph;
 ask_status ask_graph_create_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes,
                                   uint32_t flags, void *stream, ask_graph **out);
@@ -270,8 +292,12 @@ ask_status ask_plan_levels(uint32_t n, uint32_t g, uint32_t r, uint32_t B,
  * memory, a service held to a fixed memory budget.  The scratch comes from
  * arrays with static storage on the device, shared by every call: at most
  * 2^20 regions per subdivision level and 2^20 leaves (about 24 MiB on every
- * device that loads the library, held until the process exits), e.g. n up
- * to 16384 with B >= 16, or n up to 4096 with B >= 4.  A larger plan returns
+ * device that loads the library, held until the process exits).  The rule is
+ * exact: every level's bound (intervals per axis)^2, as ask_plan_levels
+ * reports it in max_regions, must be at most 2^20.  For g a power of two that
+ * divides n this holds for n up to 16384 with B >= 16 or n up to 4096 with
+ * B >= 4; a g that leaves remainder intervals can exceed it at those sizes
+ * (n = 16384, g = 17, r = 2, B = 16 does).  A larger plan returns
  * ASK_ECAPACITY before anything is launched; other argument errors return
  * ASK_EINVAL.  params->flags must be 0.  The call is asynchronous on `stream`
  * and renders into the caller's d_dwell (n*n uint32, 16-byte aligned) on the

@@ -30,6 +30,8 @@ FLAG_STAGED_COPY = 128
 FLAG_SERIAL_FILL = 256
 FLAG_INJECT_OVERFLOW = 512
 FLAG_FLOAT_FLOAT = 1024
+FLAG_PERSISTENT = 2048
+FLAG_WAIT_TEST = 4096
 
 METHODS = {"exhaustive": METHOD_EXHAUSTIVE, "ask": METHOD_ASK, "cdp2": METHOD_CDP2}
 

@@ -3,7 +3,8 @@
 Every CUDA translation unit is compiled for sm_103a only, in parallel:
 
 * ``ask_api.cu`` (host driver), ``ask_kernels.cu`` (exhaustive and ASK
-  kernels), ``ask_schemes.cu`` (the paper's SBR / MBR mappings),
+  kernels), ``ask_queue.cu`` (the persistent batch kernel over a device work
+  queue), ``ask_schemes.cu`` (the paper's SBR / MBR mappings),
   ``ask_fp64.cu`` (double-precision kernels for deep zooms) and
   ``ask_noalloc.cu`` (the allocation-free ASK entry point) as ordinary
   whole-program device code;
@@ -30,7 +31,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                       "-Xcompiler", "-ffp-contract=off", "--fmad=false", "-ftz=false",
                       "-prec-div=true", "-prec-sqrt=true", "-I", INCLUDE]
-PLAIN_UNITS = ["ask_api.cu", "ask_kernels.cu", "ask_schemes.cu", "ask_noalloc.cu", "ask_fp64.cu"]
+PLAIN_UNITS = ["ask_api.cu", "ask_kernels.cu", "ask_queue.cu", "ask_schemes.cu", "ask_noalloc.cu",
+               "ask_fp64.cu"]
 RDC_UNITS = ["ask_cdp2.cu"]
 
 

@@ -29,9 +29,28 @@ struct BatchBuffers {
     ask::DevCounters *ctr = nullptr;     // not owned when it is the context's
 };
 
+// Device scratch of a batch rendered by the persistent kernel (owned by a
+// context, or by a graph): the work queue, chunk-query states, leaf list,
+// frame table and queue state.  Queue and leaf slots are zeroed when
+// allocated, so no stale word can carry a render's epoch.
+struct QueueBuffers {
+    uint4 *items = nullptr;
+    uint32_t *aux = nullptr;
+    uint64_t item_cap = 0;
+    uint4 *rst = nullptr;
+    uint64_t rst_cap = 0;
+    uint4 *leaves = nullptr;
+    uint64_t leaf_cap = 0;
+    ask::FrameDesc *frames = nullptr;
+    uint64_t frames_cap = 0;
+    ask::QueueState *qs = nullptr;
+    ask::DevCounters *ctr = nullptr;     // not owned when it is the context's
+};
+
 struct ask_ctx {
     ask::DeviceInfo dev;
     BatchBuffers batch;
+    QueueBuffers queue;
     ask::FrameDesc *h_frames = nullptr;  // pinned staging of the frame table
     uint64_t h_frames_cap = 0;
     cudaEvent_t frames_copied = nullptr; // the staging buffer may be rewritten after it
@@ -74,6 +93,8 @@ struct ask_ctx {
 struct ask_graph {
     int device = 0;
     BatchBuffers buf;
+    QueueBuffers qbuf;
+    bool persistent = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -343,6 +364,8 @@ ask_status latched_error(ask_ctx *ctx, uint32_t err)
         return set_err(ctx, ASK_ECUDA, "a device-side child launch failed (pending-launch limit?)");
     if (err & (ERR_OLT_OVERFLOW | ERR_LEAF_OVERFLOW))
         return set_err(ctx, ASK_EOVERFLOW, "a region table overflowed its capacity");
+    if (err & ERR_TIMEOUT)
+        return set_err(ctx, ASK_ETIMEOUT, "a bounded wait of the persistent batch kernel gave up");
     if (err)
         return set_err(ctx, ASK_EOVERFLOW, "device error bits 0x%x", err);
     return ASK_OK;
@@ -512,6 +535,11 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
                 return set_err(ctx, ASK_EUNSUPPORTED, "cannot set the device runtime's pending-launch limit");
             cudaGetLastError();  // a refused raise is not sticky
         }
+        // tail launches without MBR: one device-launched grid per depth over
+        // a list of that depth's regions (the region tables hold the lists)
+        const bool fnf = (p.flags & ASK_FLAG_CDP2_FIRE_AND_FORGET) != 0;
+        if (!fnf && !mbr && (st = reserve_ask(ctx, plan)) != ASK_OK)
+            return st;
         mk.at(0, s);
         if ((e = launch_init(nullptr, nullptr, ctx->ctr, n, 1, 0, 0, 0, s)) != cudaSuccess)
             return cuda_err(ctx, e, "init kernel");
@@ -525,6 +553,9 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.count = count ? 1u : 0u;
         a.fire_and_forget = (p.flags & ASK_FLAG_CDP2_FIRE_AND_FORGET) ? 1u : 0u;
         a.mbr = mbr ? 1u : 0u;
+        a.list[0] = (!fnf && !mbr) ? ctx->olt[0] : nullptr;
+        a.list[1] = (!fnf && !mbr) ? ctx->olt[1] : nullptr;
+        a.list_cap = (!fnf && !mbr) ? (uint32_t)ctx->olt_cap : 0u;
         a.ctr = ctx->ctr;
         if ((e = launch_cdp2(a, p.g, plan.side[0], p.block_x, p.block_y, s)) != cudaSuccess)
             return cuda_err(ctx, e, "CDP2 root kernel");
@@ -691,7 +722,19 @@ struct BatchPlan {
     uint32_t chunks[ASK_MAX_LEVELS] = {};  // chunks per region at each level (max over frames)
     uint64_t olt_need = 0, leaf_need = 0, rst_need = 0, fill_need = 0;
     uint32_t total0 = 0;
+    // the persistent batch kernel: queue items (every level's chunk items and
+    // fill bands of every frame), chunk states, level-0 items and states
+    uint64_t q_items = 0, q_states = 0, q_total0 = 0, q_states0 = 0;
 };
+
+// Chunk items per region of a level of side s in the persistent batch
+// kernel: kChunkPxQueue perimeter pixels each, at most kMaxChunksQueue.
+uint32_t queue_chunks(uint32_t s)
+{
+    const uint64_t per = (s <= 2u) ? (uint64_t)s * s : 4ull * s - 4ull;
+    const uint64_t c = (per + kChunkPxQueue - 1) / kChunkPxQueue;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(c, kMaxChunksQueue));
+}
 
 ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, uint32_t flags,
                       uint32_t allowed_flags, BatchPlan &bp)
@@ -734,14 +777,27 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
         d.s0 = plan.side[0];
         d.axis0 = plan.axis0;
         d.olt0_offset = (uint32_t)total0;
+        d.item0 = (uint32_t)std::min<uint64_t>(bp.q_total0, 0xffffffffull);
+        d.state0 = (uint32_t)std::min<uint64_t>(bp.q_states0, 0xffffffffull);
         for (uint32_t i = 0; i < plan.levels; ++i) {
             d.side[i] = plan.side[i];
+            d.chunks[i] = queue_chunks(plan.side[i]);
             level_regions[i] += plan.max_regions[i];
             if (plan.chunks[i] > bp.chunks[i])
                 bp.chunks[i] = plan.chunks[i];
-            if ((uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea)
-                bp.fill_need += plan.max_regions[i] * fill_band_count(plan.side[i], plan.side[i]);
+            bp.q_items += plan.max_regions[i] * d.chunks[i];
+            if (d.chunks[i] > 1u)
+                bp.q_states += plan.max_regions[i];
+            if ((uint64_t)plan.side[i] * plan.side[i] > kInPlaceFillArea) {
+                const uint64_t bands = plan.max_regions[i] * fill_band_count(plan.side[i], plan.side[i]);
+                bp.fill_need += bands;
+                bp.q_items += bands;
+            }
         }
+        const uint64_t regions0 = (uint64_t)plan.axis0 * plan.axis0;
+        bp.q_total0 += regions0 * d.chunks[0];
+        if (d.chunks[0] > 1u)
+            bp.q_states0 += regions0;
         bp.leaf_need += plan.max_regions[plan.levels - 1];
         total0 += (uint64_t)plan.axis0 * plan.axis0;
         if (plan.levels > bp.L)
@@ -758,6 +814,8 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
     }
     if (bp.leaf_need >= 0xffffffffull || bp.fill_need >= 0xffffffffull)
         return set_err(ctx, ASK_EINVAL, "batch too large");
+    if ((flags & ASK_FLAG_PERSISTENT) && (bp.q_items >= 0xffffffffull || bp.q_states >= 0xffffffffull))
+        return set_err(ctx, ASK_EINVAL, "batch too large for the persistent kernel's work queue");
     bp.total0 = (uint32_t)total0;
     return ASK_OK;
 }
@@ -873,7 +931,7 @@ ask_status enqueue_batch(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &b
 }
 
 // Copy the frame table through the context's pinned staging buffer.
-ask_status upload_frames(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &bp, cudaStream_t s)
+ask_status upload_frames(ask_ctx *ctx, FrameDesc *dst, const BatchPlan &bp, cudaStream_t s)
 {
     const uint64_t nf = bp.desc.size();
     cudaError_t e;
@@ -892,11 +950,104 @@ ask_status upload_frames(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &b
                                    cudaSuccess)
         return cuda_err(ctx, e, "cudaEventCreate");
     std::memcpy(ctx->h_frames, bp.desc.data(), nf * sizeof(FrameDesc));
-    if ((e = cudaMemcpyAsync(b.frames, ctx->h_frames, nf * sizeof(FrameDesc), cudaMemcpyHostToDevice, s)) !=
+    if ((e = cudaMemcpyAsync(dst, ctx->h_frames, nf * sizeof(FrameDesc), cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
         return cuda_err(ctx, e, "copying the frame table");
     if ((e = cudaEventRecord(ctx->frames_copied, s)) != cudaSuccess)
         return cuda_err(ctx, e, "cudaEventRecord");
+    return ASK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches rendered by the persistent kernel over a device work queue
+// ---------------------------------------------------------------------------
+
+// Grow a queue array, zeroing new memory so that no word in it can carry a
+// render's epoch.
+template <typename T>
+ask_status grow_zeroed(ask_ctx *ctx, T **buf, uint64_t *cap, uint64_t need, const char *what)
+{
+    if (need <= *cap)
+        return ASK_OK;
+    ask_status st = grow(ctx, buf, cap, need, what);
+    if (st != ASK_OK)
+        return st;
+    cudaError_t e = cudaMemset(*buf, 0, need * sizeof(T));
+    return e == cudaSuccess ? ASK_OK : cuda_err(ctx, e, what);
+}
+
+ask_status reserve_queue(ask_ctx *ctx, QueueBuffers &b, const BatchPlan &bp, bool own_counters)
+{
+    ask_status st;
+    if (bp.q_items > b.item_cap) {
+        uint64_t c = b.item_cap;
+        if ((st = grow_zeroed(ctx, &b.items, &c, bp.q_items, "cudaMalloc(work queue)")) != ASK_OK ||
+            (st = grow(ctx, &b.aux, &b.item_cap, bp.q_items, "cudaMalloc(work queue)")) != ASK_OK) {
+            b.item_cap = 0;
+            return st;
+        }
+    }
+    if ((st = grow(ctx, &b.rst, &b.rst_cap, std::max<uint64_t>(bp.q_states, 1), "cudaMalloc(query states)")) !=
+        ASK_OK)
+        return st;
+    if ((st = grow_zeroed(ctx, &b.leaves, &b.leaf_cap, bp.leaf_need, "cudaMalloc(leaf list)")) != ASK_OK)
+        return st;
+    if ((st = grow(ctx, &b.frames, &b.frames_cap, (uint64_t)bp.desc.size(), "cudaMalloc(frame table)")) != ASK_OK)
+        return st;
+    if (!b.qs) {
+        cudaError_t e = cudaMalloc(&b.qs, sizeof(QueueState));
+        if (e == cudaSuccess)
+            e = cudaMemset(b.qs, 0, sizeof(QueueState));
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaMalloc(queue state)");
+    }
+    if (own_counters && !b.ctr) {
+        cudaError_t e = cudaMalloc(&b.ctr, sizeof(DevCounters));
+        if (e == cudaSuccess)
+            e = cudaMemset(b.ctr, 0, sizeof(DevCounters));
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "cudaMalloc(batch counters)");
+    }
+    return ASK_OK;
+}
+
+void free_queue(QueueBuffers &b, bool own_counters)
+{
+    void *bufs[] = {b.items, b.aux, b.rst, b.leaves, b.frames, b.qs};
+    for (void *p : bufs)
+        if (p)
+            cudaFree(p);
+    if (own_counters && b.ctr)
+        cudaFree(b.ctr);
+    b = QueueBuffers();
+}
+
+// The two launches of a persistent batch: the init kernel and the
+// persistent kernel; the frame table must already be on the device.
+ask_status enqueue_queue(ask_ctx *ctx, const QueueBuffers &b, const BatchPlan &bp, uint32_t flags,
+                         cudaStream_t s, uint32_t *launches)
+{
+    QueueArgs q;
+    q.items = b.items;
+    q.aux = b.aux;
+    q.item_cap = (uint32_t)b.item_cap;
+    q.rst = b.rst;
+    q.rst_cap = (uint32_t)b.rst_cap;
+    q.leaves = b.leaves;
+    q.leaf_cap = (uint32_t)b.leaf_cap;
+    q.frames = b.frames;
+    q.ctr = b.ctr;
+    q.qs = b.qs;
+    q.regions0 = bp.total0;
+    q.total0 = (uint32_t)bp.q_total0;
+    q.states0 = (uint32_t)bp.q_states0;
+    q.chunk_px = kChunkPxQueue;
+    q.wait_limit = (flags & ASK_FLAG_WAIT_TEST) ? 0u : kQueueWaitLimit;
+    cudaError_t e = launch_queue(q, (uint32_t)bp.desc.size(), (flags & ASK_FLAG_COUNT) != 0, ctx->dev.sms, s);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "persistent batch kernel");
+    if (launches)
+        *launches = 2;
     return ASK_OK;
 }
 
@@ -966,6 +1117,7 @@ void ask_ctx_destroy(ask_ctx *ctx)
     if (ctx->fills)
         cudaFree(ctx->fills);
     free_batch(ctx->batch, false);
+    free_queue(ctx->queue, false);
     if (ctx->h_frames)
         cudaFreeHost(ctx->h_frames);
     if (ctx->frames_copied)
@@ -1181,16 +1333,28 @@ ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nfra
 {
     if (!ctx)
         return ASK_EINVAL;
+    const bool persistent = (flags & ASK_FLAG_PERSISTENT) != 0;
+    if ((flags & ASK_FLAG_WAIT_TEST) && !persistent)
+        return set_err(ctx, ASK_EINVAL, "ASK_FLAG_WAIT_TEST needs ASK_FLAG_PERSISTENT");
     BatchPlan bp;
-    ask_status st = plan_batch(ctx, frames, nframes, flags, ASK_FLAG_COUNT | ASK_FLAG_EXACT_BORDERS, bp);
+    ask_status st = plan_batch(ctx, frames, nframes, flags,
+                               persistent ? (ASK_FLAG_COUNT | ASK_FLAG_PERSISTENT | ASK_FLAG_WAIT_TEST)
+                                          : (ASK_FLAG_COUNT | ASK_FLAG_EXACT_BORDERS),
+                               bp);
     if (st != ASK_OK)
         return st;
     if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
         return set_err(ctx, ASK_ECUDA, "cudaSetDevice");
     if ((st = ensure_counters(ctx)) != ASK_OK)
         return st;
-    ctx->batch.ctr = ctx->ctr;
-    if ((st = reserve_batch(ctx, ctx->batch, bp, false)) != ASK_OK)
+    if (persistent) {
+        ctx->queue.ctr = ctx->ctr;
+        st = reserve_queue(ctx, ctx->queue, bp, false);
+    } else {
+        ctx->batch.ctr = ctx->ctr;
+        st = reserve_batch(ctx, ctx->batch, bp, false);
+    }
+    if (st != ASK_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (stats) {
@@ -1198,12 +1362,16 @@ ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nfra
         if ((st = ensure_events(ctx)) != ASK_OK)
             return st;
     }
-    if ((st = upload_frames(ctx, ctx->batch, bp, s)) != ASK_OK)
+    if ((st = upload_frames(ctx, persistent ? ctx->queue.frames : ctx->batch.frames, bp, s)) != ASK_OK)
         return st;
     if (stats)
         cudaEventRecord(ctx->ev[0], s);
     uint32_t launches = 0;
-    if ((st = enqueue_batch(ctx, ctx->batch, bp, flags, s, &launches)) != ASK_OK)
+    if (persistent)
+        st = enqueue_queue(ctx, ctx->queue, bp, flags, s, &launches);
+    else
+        st = enqueue_batch(ctx, ctx->batch, bp, flags, s, &launches);
+    if (st != ASK_OK)
         return st;
     if (stats) {
         cudaEventRecord(ctx->ev[1], s);
@@ -1236,8 +1404,10 @@ ask_status ask_graph_create_batch(ask_ctx *ctx, const ask_frame *frames, uint32_
     if (!ctx || !out)
         return ASK_EINVAL;
     *out = nullptr;
+    const bool persistent = (flags & ASK_FLAG_PERSISTENT) != 0;
     BatchPlan bp;
-    ask_status st = plan_batch(ctx, frames, nframes, flags, ASK_FLAG_EXACT_BORDERS, bp);
+    ask_status st = plan_batch(ctx, frames, nframes, flags,
+                               persistent ? ASK_FLAG_PERSISTENT : ASK_FLAG_EXACT_BORDERS, bp);
     if (st != ASK_OK)
         return st;
     if (cudaSetDevice(ctx->dev.device) != cudaSuccess)
@@ -1246,31 +1416,44 @@ ask_status ask_graph_create_batch(ask_ctx *ctx, const ask_frame *frames, uint32_
     if (!g)
         return ASK_ENOMEM;
     g->device = ctx->dev.device;
+    g->persistent = persistent;
+    auto release = [](ask_graph *gr) {
+        if (gr->exec)
+            cudaGraphExecDestroy(gr->exec);
+        if (gr->graph)
+            cudaGraphDestroy(gr->graph);
+        free_batch(gr->buf, true);
+        free_queue(gr->qbuf, true);
+        delete gr;
+    };
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
-    if ((st = reserve_batch(ctx, g->buf, bp, true)) != ASK_OK ||
-        (st = upload_frames(ctx, g->buf, bp, s)) != ASK_OK) {
-        free_batch(g->buf, true);
-        delete g;
+    if (persistent)
+        st = reserve_queue(ctx, g->qbuf, bp, true);
+    else
+        st = reserve_batch(ctx, g->buf, bp, true);
+    if (st == ASK_OK)
+        st = upload_frames(ctx, persistent ? g->qbuf.frames : g->buf.frames, bp, s);
+    if (st != ASK_OK) {
+        release(g);
         return st;
     }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
-        free_batch(g->buf, true);
-        delete g;
+        release(g);
         return cuda_err(ctx, e, "cudaStreamSynchronize");
     }
     // capture on a private stream so the caller's stream is never in capture mode
     cudaStream_t cs = nullptr;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
-        free_batch(g->buf, true);
-        delete g;
+        release(g);
         return cuda_err(ctx, e, "cudaStreamCreate");
     }
     st = ASK_OK;
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
         st = cuda_err(ctx, e, "cudaStreamBeginCapture");
     } else {
-        const ask_status est = enqueue_batch(ctx, g->buf, bp, flags, cs, nullptr);
+        const ask_status est = persistent ? enqueue_queue(ctx, g->qbuf, bp, flags, cs, nullptr)
+                                          : enqueue_batch(ctx, g->buf, bp, flags, cs, nullptr);
         e = cudaStreamEndCapture(cs, &g->graph);
         if (est != ASK_OK)
             st = est;
@@ -1281,12 +1464,7 @@ ask_status ask_graph_create_batch(ask_ctx *ctx, const ask_frame *frames, uint32_
     }
     cudaStreamDestroy(cs);
     if (st != ASK_OK) {
-        if (g->exec)
-            cudaGraphExecDestroy(g->exec);
-        if (g->graph)
-            cudaGraphDestroy(g->graph);
-        free_batch(g->buf, true);
-        delete g;
+        release(g);
         return st;
     }
     *out = g;
@@ -1312,6 +1490,7 @@ void ask_graph_destroy(ask_graph *g)
     if (g->graph)
         cudaGraphDestroy(g->graph);
     free_batch(g->buf, true);
+    free_queue(g->qbuf, true);
     delete g;
 }
 

@@ -68,26 +68,25 @@ __global__ void __launch_bounds__(1024) cdp2_pixel_kernel(CdpArgs a, Region g)
     }
 }
 
-// One CTA = one region: child (blockIdx.x, blockIdx.y) of side `side` inside
-// the parent rectangle (px0, py0, pw, ph).  The root grid's "parent" is the
-// whole image and its children are the g x g initial regions.
+// Shared memory of a region's CTA besides the perimeter stage.
+struct CdpShared {
+    uint32_t red_min[32], red_max[32];
+    uint32_t s_min, s_max, s_flag, s_w, s_base;
+};
+
+// Tail launches without MBR take the per-depth lists.
+__device__ __forceinline__ bool list_mode(const CdpArgs &a) { return !a.fire_and_forget && !a.mbr; }
+
 __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t px0, uint32_t py0,
                                                            uint32_t pw, uint32_t ph, uint32_t side,
-                                                           uint32_t level)
+                                                           uint32_t level);
+
+// The work of one region g of nominal side `side` at depth `level`, by one
+// CTA: the exploration query, then a fill, a split (a child grid, or the
+// next depth's list) or the leaf's pixels.
+__device__ __forceinline__ void cdp2_region(const CdpArgs &a, const Region &g, uint32_t side,
+                                            uint32_t level, uint32_t *stage, CdpShared &sh)
 {
-    extern __shared__ uint32_t stage[];
-    __shared__ uint32_t red_min[32], red_max[32];
-    __shared__ uint32_t s_min, s_max, s_flag, s_w;
-
-    const uint32_t x0 = px0 + blockIdx.x * side, y0 = py0 + blockIdx.y * side;
-    if (x0 >= px0 + pw || y0 >= py0 + ph)
-        return;  // empty child (uniform over the CTA)
-    Region g;
-    g.x0 = x0;
-    g.y0 = y0;
-    g.w = min(side, px0 + pw - x0);
-    g.h = min(side, py0 + ph - y0);
-
     const uint32_t T = blockDim.x * blockDim.y;
     const uint32_t tid = threadIdx.x + threadIdx.y * blockDim.x;
     const uint32_t lane = tid & 31u, wid = tid >> 5, nw = T >> 5;
@@ -101,12 +100,12 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
     if (split) {
         // exploration query that stops at the first difference
         if (tid == 0) {
-            s_flag = 0u;
-            s_w = 0xffffffffu;
+            sh.s_flag = 0u;
+            sh.s_w = 0xffffffffu;
         }
         __syncthreads();
         uint32_t wv = 0;
-        const bool uni = cta_perimeter_uniform(a.pm, a.max_dwell, g, tid, T, &s_flag, &s_w, &wv, it);
+        const bool uni = cta_perimeter_uniform(a.pm, a.max_dwell, g, tid, T, &sh.s_flag, &sh.s_w, &wv, it);
         dmin = wv;
         dmax = uni ? wv : wv + 1u;
     } else {
@@ -130,23 +129,23 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
         dmin = __reduce_min_sync(kFull, dmin);
         dmax = __reduce_max_sync(kFull, dmax);
         if (lane == 0) {
-            red_min[wid] = dmin;
-            red_max[wid] = dmax;
+            sh.red_min[wid] = dmin;
+            sh.red_max[wid] = dmax;
         }
         __syncthreads();
         if (wid == 0) {
-            uint32_t m0 = lane < nw ? red_min[lane] : 0xffffffffu;
-            uint32_t m1 = lane < nw ? red_max[lane] : 0u;
+            uint32_t m0 = lane < nw ? sh.red_min[lane] : 0xffffffffu;
+            uint32_t m1 = lane < nw ? sh.red_max[lane] : 0u;
             m0 = __reduce_min_sync(kFull, m0);
             m1 = __reduce_max_sync(kFull, m1);
             if (lane == 0) {
-                s_min = m0;
-                s_max = m1;
+                sh.s_min = m0;
+                sh.s_max = m1;
             }
         }
         __syncthreads();
-        dmin = s_min;
-        dmax = s_max;
+        dmin = sh.s_min;
+        dmax = sh.s_max;
     }
 
     if (dmin == dmax) {
@@ -168,7 +167,23 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
         if (tid == 0)
             atomicAdd(&a.ctr->fills[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
     } else {
-        if (split) {
+        if (split && list_mode(a)) {
+            // append the children to the next depth's list
+            const uint32_t cx = min(a.r, ceil_div_u32(g.w, sc));
+            const uint32_t cy = min(a.r, ceil_div_u32(g.h, sc));
+            if (tid == 0) {
+                atomicAdd(&a.ctr->subdivs[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
+                sh.s_base = atomicAdd(&a.ctr->count[level + 1u], cx * cy);
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < cx * cy; j += T) {
+                const uint32_t slot = sh.s_base + j;
+                if (slot < a.list_cap)
+                    a.list[(level + 1u) & 1u][slot] = child_region(g, sc, a.r, j);
+                else
+                    atomicOr(&a.ctr->error, ERR_OLT_OVERFLOW);
+            }
+        } else if (split) {
             if (tid == 0) {
                 atomicAdd(&a.ctr->subdivs[min(level, (uint32_t)ASK_MAX_LEVELS - 1u)], 1u);
                 const uint32_t cx = min(a.r, ceil_div_u32(g.w, sc));
@@ -231,6 +246,64 @@ __global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t p
     }
 }
 
+__global__ void __launch_bounds__(1024) cdp2_list_kernel(CdpArgs a, uint32_t side, uint32_t level);
+
+// The last CTA of a depth's grid to finish tail-launches one grid over the
+// next depth's list (list mode only); `nblocks` CTAs count.
+__device__ __forceinline__ void cdp2_grid_done(const CdpArgs &a, uint32_t side, uint32_t level,
+                                               uint32_t nblocks)
+{
+    __syncthreads();  // every append of this CTA is issued
+    if (threadIdx.x + threadIdx.y * blockDim.x != 0u)
+        return;
+    __threadfence();
+    if (atomicAdd(&a.ctr->work[level], 1u) != nblocks - 1u)
+        return;
+    __threadfence();
+    const uint32_t cnt = min(atomicAdd(&a.ctr->count[level + 1u], 0u), a.list_cap);
+    if (cnt == 0u)
+        return;
+    const uint32_t sc = ceil_div_u32(side, a.r);
+    const size_t smem = (size_t)min(4u * sc, kStageMax) * sizeof(uint32_t);
+    cdp2_list_kernel<<<cnt, dim3(blockDim.x, blockDim.y), smem, cudaStreamTailLaunch>>>(a, sc, level + 1u);
+    if (cudaGetLastError() != cudaSuccess)
+        atomicOr(&a.ctr->error, ERR_DEVICE_LAUNCH);
+}
+
+// One CTA = one region: child (blockIdx.x, blockIdx.y) of side `side` inside
+// the parent rectangle (px0, py0, pw, ph).  The root grid's "parent" is the
+// whole image and its children are the g x g initial regions.
+__global__ void __launch_bounds__(1024) cdp2_region_kernel(CdpArgs a, uint32_t px0, uint32_t py0,
+                                                           uint32_t pw, uint32_t ph, uint32_t side,
+                                                           uint32_t level)
+{
+    extern __shared__ uint32_t stage[];
+    __shared__ CdpShared sh;
+    const uint32_t x0 = px0 + blockIdx.x * side, y0 = py0 + blockIdx.y * side;
+    if (x0 < px0 + pw && y0 < py0 + ph) {  // else an empty child (uniform over the CTA)
+        Region g;
+        g.x0 = x0;
+        g.y0 = y0;
+        g.w = min(side, px0 + pw - x0);
+        g.h = min(side, py0 + ph - y0);
+        cdp2_region(a, g, side, level, stage, sh);
+    }
+    if (list_mode(a))
+        cdp2_grid_done(a, side, level, gridDim.x * gridDim.y);
+}
+
+// One CTA per region of depth `level`'s list (list mode).
+__global__ void __launch_bounds__(1024) cdp2_list_kernel(CdpArgs a, uint32_t side, uint32_t level)
+{
+    extern __shared__ uint32_t stage[];
+    __shared__ CdpShared sh;
+    const Region g = unpack_region(a.list[level & 1u][blockIdx.x]);
+    cdp2_region(a, g, side, level, stage, sh);
+    cdp2_grid_done(a, side, level, gridDim.x);
+}
+
+bool list_mode_host(const CdpArgs &a) { return !a.fire_and_forget && !a.mbr; }
+
 }  // namespace
 
 cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, uint32_t by,
@@ -239,9 +312,12 @@ cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, 
     const uint32_t axis0 = (a.n + s0 - 1) / s0;  // non-empty initial regions per axis
     (void)g;
     const size_t smem = (size_t)min(4u * s0, kStageMax) * sizeof(uint32_t);
-    if (smem > 48 * 1024)
+    if (smem > 48 * 1024 || list_mode_host(a)) {
         cudaFuncSetAttribute(cdp2_region_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kStageMax * sizeof(uint32_t)));
+        cudaFuncSetAttribute(cdp2_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kStageMax * sizeof(uint32_t)));
+    }
     cdp2_region_kernel<<<dim3(axis0, axis0), dim3(bx, by), smem, s>>>(a, 0u, 0u, a.n, a.n, s0, 0u);
     return cudaGetLastError();
 }

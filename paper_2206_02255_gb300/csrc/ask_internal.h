@@ -41,6 +41,7 @@ enum : uint32_t {
     ERR_LEAF_OVERFLOW = 2u,
     ERR_DEVICE_LAUNCH = 4u,
     ERR_DEPTH = 8u,
+    ERR_TIMEOUT = 16u,  // a bounded wait of the persistent batch kernel gave up
 };
 
 // One level of the subdivision plan.
@@ -85,6 +86,10 @@ struct FrameDesc {
     uint32_t olt0_offset; // first level-0 record of this frame
     uint32_t pad_;
     uint32_t side[ASK_MAX_LEVELS];  // region side at each level
+    // persistent batch kernel (ask_queue.cu) only
+    uint32_t item0;       // first level-0 queue item of this frame
+    uint32_t state0;      // first level-0 chunk state of this frame
+    uint32_t chunks[ASK_MAX_LEVELS];  // perimeter chunks (queue items) per region at each level
 };
 
 struct LevelArgs {
@@ -176,6 +181,49 @@ struct LeafArgs {
 cudaError_t launch_leaf(const LeafArgs &a, uint32_t bx, uint32_t by, bool count, bool tiled,
                         bool batch, int sms, cudaStream_t s);
 
+// ---- the persistent batch kernel of ask_queue.cu -------------------------
+// Queue state of one render, next to its items.  `epoch` survives between
+// renders (the render's items carry epoch + 1); the init kernel resets the
+// rest.
+struct QueueState {
+    uint32_t epoch;      // epoch of the last finished render
+    uint32_t head;       // next region ticket
+    uint32_t tail;       // queue slots reserved
+    uint32_t pending;    // items pushed and not yet finished
+    uint32_t done;       // = the render's epoch once pending reached 0
+    uint32_t states;     // chunk-query states handed out
+    uint32_t leaf_head;  // next leaf ticket
+    uint32_t exited;     // warps that have left the persistent kernel
+};
+
+struct QueueArgs {
+    uint4 *items;         // {origin, extent, tag, epoch}: tag = frame | level << 20 | kind << 25 | chunk << 26
+    uint32_t *aux;        // per item: chunk-state index (region) or dwell (fill band)
+    uint32_t item_cap;
+    uint4 *rst;           // chunk-query states {common dwell, differs, chunks done, -}
+    uint32_t rst_cap;
+    uint4 *leaves;        // leaf list {origin, extent, frame, epoch}
+    uint32_t leaf_cap;
+    const FrameDesc *frames;
+    DevCounters *ctr;
+    QueueState *qs;
+    uint32_t regions0;    // level-0 regions of all frames
+    uint32_t total0;      // level-0 items of all frames
+    uint32_t states0;     // level-0 chunk states of all frames
+    uint32_t chunk_px;    // perimeter pixels per chunk item (a region's last chunks may be longer)
+    uint32_t wait_limit;  // idle polls in a row before a warp reports ERR_TIMEOUT
+};
+// Perimeter pixels per chunk item and the most chunk items per region of the
+// persistent batch kernel (a region whose perimeter needs more takes longer
+// chunks; the tag has 6 bits for the chunk).
+constexpr uint32_t kChunkPxQueue = 128;
+constexpr uint32_t kMaxChunksQueue = 16;
+// Idle polls in a row (with __nanosleep back-off of up to 256 ns, reset
+// whenever the queue or the leaf list moves) before a warp gives up.
+constexpr uint32_t kQueueWaitLimit = 1u << 26;
+// Init kernel (one block per frame) and the persistent kernel, on `s`.
+cudaError_t launch_queue(const QueueArgs &q, uint32_t nframes, bool count, int sms, cudaStream_t s);
+
 // ---- kernels of ask_cdp2.cu ----------------------------------------------
 struct CdpArgs {
     uint32_t *map;
@@ -186,6 +234,11 @@ struct CdpArgs {
     uint32_t count;       // ASK_FLAG_COUNT
     uint32_t fire_and_forget;  // children into cudaStreamFireAndForget, not the tail stream
     uint32_t mbr;              // DP-MBR: fills and leaf pixels by child grids
+    // tail launches without MBR: the regions a grid splits into are appended
+    // to list[(level + 1) & 1] and the grid's last CTA tail-launches one grid
+    // over all of them
+    uint2 *list[2];
+    uint32_t list_cap;
     DevCounters *ctr;
 };
 cudaError_t launch_cdp2(const CdpArgs &a, uint32_t g, uint32_t s0, uint32_t bx, uint32_t by,

@@ -38,24 +38,15 @@
 
 #include "ask_device.cuh"
 #include "ask_internal.h"
+#include "ask_work.cuh"
 
 namespace ask {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kWarpStage = 512;  // staged perimeter pixels per warp (exact last level)
-constexpr uint32_t kNone = 0xffffffffu;
 
 enum : uint32_t { KIND_NONE = 0, KIND_FILL = 1, KIND_SPLIT = 2, KIND_LEAF = 3, KIND_FILL_LATER = 4 };
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
 // ---------------------------------------------------------------------------
 // Exhaustive: one thread per pixel over a flat grid of block_x x block_y
@@ -109,63 +100,6 @@ __global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, 
         if (rst0 != nullptr)
             rst0[k] = make_uint4(kNone, 0u, 0u, 0u);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Region records: uint2 for one frame, uint4 (with the frame id) for a batch.
-// ---------------------------------------------------------------------------
-template <bool BATCH>
-struct Rec;
-template <>
-struct Rec<false> {
-    using T = uint2;
-    static __device__ __forceinline__ Region region(T e) { return unpack_region(e); }
-    static __device__ __forceinline__ uint32_t frame(T) { return 0u; }
-    static __device__ __forceinline__ T child(T, uint2 c) { return c; }
-};
-template <>
-struct Rec<true> {
-    using T = uint4;
-    static __device__ __forceinline__ Region region(T e) { return unpack_region(make_uint2(e.x, e.y)); }
-    static __device__ __forceinline__ uint32_t frame(T e) { return e.z; }
-    static __device__ __forceinline__ T child(T p, uint2 c) { return make_uint4(c.x, c.y, p.z, 0u); }
-};
-
-// The parameters of the frame a region belongs to, at one level.
-struct FView {
-    uint32_t *map;
-    PixelMap pm;
-    uint32_t n, max_dwell, side, child_side, r;
-    bool split;
-};
-
-__device__ __forceinline__ FView view_single(const LevelArgs &a)
-{
-    FView v;
-    v.map = a.map;
-    v.pm = a.pm;
-    v.n = a.n;
-    v.max_dwell = a.max_dwell;
-    v.side = a.side;
-    v.child_side = a.child_side;
-    v.r = a.r;
-    v.split = a.split != 0u;
-    return v;
-}
-
-__device__ __forceinline__ FView view_frame(const FrameDesc *frames, uint32_t f, uint32_t level)
-{
-    const FrameDesc &d = frames[f];
-    FView v;
-    v.map = d.map;
-    v.pm = d.pm;
-    v.n = d.n;
-    v.max_dwell = d.max_dwell;
-    v.r = d.r;
-    v.side = d.side[level];
-    v.child_side = ceil_div_u32(v.side, v.r);
-    v.split = level + 1u < d.levels;
-    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -271,97 +205,6 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH>
     }
     b.kind = KIND_NONE;
     b.nchild = 0;
-}
-
-// Rounds between issuing a state load and using it, for one frame.  A
-// batch keeps enough warps resident to hide the load, and there a late
-// stop costs more than the wait, so it uses the value one round later.
-constexpr uint32_t kPollLag = 8;
-
-// One chunk [k0, k1) of a large region's perimeter, queried by one warp.  The
-// region's state st: x = common dwell found so far (kNone: none yet),
-// y = 1 once two dwells are known to differ, z = chunks finished.  Chunks of
-// the same region run on other warps at the same time and stop as soon as
-// one of them has set y.
-template <bool BATCH>
-__device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uint32_t k0,
-                                            uint32_t k1, uint4 *st, uint32_t lane,
-                                            unsigned long long &it)
-{
-    const volatile uint32_t *ps = reinterpret_cast<const volatile uint32_t *>(st);
-    for (uint32_t base = k0; base < k1; base += 32u) {
-        // the state load is issued first; the group's set-up hides its latency
-        uint32_t sx = 0, sy = 0;
-        if (lane == 0) {
-            sx = ps[0];
-            sy = ps[1];
-        }
-        const uint32_t k = base + lane;
-        const bool active = k < k1;
-        const unsigned amask = __ballot_sync(kFull, active);
-        uint32_t px = g.x0, py = g.y0;
-        if (active)
-            perimeter_pixel(g, k, px, py);
-        Orbit o = orbit_start(pixel_c(a.pm, px, py));
-        uint32_t stt = active ? ORBIT_RUN : ORBIT_DONE;
-        bool differ = false, stop = false;
-        uint2 v = make_uint2(__shfl_sync(kFull, sx, 0), __shfl_sync(kFull, sy, 0));
-        if (v.y)
-            return;
-        // A state load is issued every kPollLag rounds (every round in a
-        // batch) and consumed that many rounds later, so its L2 latency
-        // hides behind the updates of those rounds; a stale value is
-        // harmless (the common dwell is set once, the flag only rises).
-        uint32_t nx = v.x, ny = v.y, lag = 0;
-        for (;;) {
-            if (lag == 0 && lane == 0) {
-                nx = ps[0];
-                ny = ps[1];
-            }
-            const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
-            if (stt == ORBIT_RUN)
-                stt = orbit_step<kQueryRoundLarge>(o, limit);
-            const unsigned dm = __ballot_sync(kFull, stt != ORBIT_RUN) & amask;
-            if (dm == amask)
-                break;
-            if (dm) {
-                differ = true;
-                break;
-            }
-            if (++lag == (BATCH ? 1u : kPollLag)) {
-                lag = 0;
-                v.x = __shfl_sync(kFull, nx, 0);
-                v.y = __shfl_sync(kFull, ny, 0);
-                if (v.y) {
-                    stop = true;
-                    break;
-                }
-            }
-        }
-        if (!stop && !differ && stt == ORBIT_PEND)
-            orbit_resolve<kQueryRoundLarge>(o);
-        if (active)
-            it += o.d;
-        if (stop)
-            return;
-        if (differ) {
-            if (lane == 0)
-                atomicExch(&st->y, 1u);
-            return;
-        }
-        const uint32_t vmin = __reduce_min_sync(kFull, active ? o.d : kNone);
-        const uint32_t vmax = __reduce_max_sync(kFull, active ? o.d : 0u);
-        if (lane == 0) {
-            if (vmin != vmax) {
-                atomicExch(&st->y, 1u);
-            } else {
-                const uint32_t old = atomicCAS(&st->x, kNone, vmin);
-                if (old != kNone && old != vmin)
-                    atomicExch(&st->y, 1u);
-            }
-        }
-        __syncwarp();
-    }
 }
 
 // One chunk [k0, k1) of a large last-level region with exact perimeters:
@@ -630,202 +473,65 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 }
 
 // ---------------------------------------------------------------------------
-// Leaf kernel with lane refill (default).  Leaf pixels near the set's
-// boundary have dwells from a handful of updates to max_dwell side by side,
-// so a warp that owned 32 fixed pixels would idle most lanes while one orbit
-// runs on.  Here each warp takes leaves from a device counter and feeds their
-// pixels to its lanes one at a time:
-//  * every round, each busy lane advances its orbit by one unchecked block
-//    (see dwell()); a lane whose block ends escaped, or that has fewer than a
-//    block's worth of updates left, parks (saved state, count, pixel) in the
-//    warp's buffer in shared memory and takes a new pixel at once;
+// Leaf kernel (default): a coherent first pass over fresh pixels, then lane
+// refill for the orbits that survive it.
+//
+// Leaf pixels lie near the set's boundary: their dwells run from a handful
+// of updates to max_dwell side by side (at n = 16384 the median leaf pixel
+// escapes after 19 updates, 71% within 32, while the 5% that reach max_dwell
+// hold two thirds of the updates).  A warp that owned 32 fixed pixels would
+// idle most lanes while one orbit runs on, so each warp takes leaves from a
+// device counter and works in two stages:
+//  * pre-pass: 32 fresh pixels at a time, one per lane, all lanes in
+//    lockstep, run their first kPrePass updates in unchecked blocks of
+//    kPreBlock with one test per block (see dwell()).  An orbit that escapes
+//    there is resolved on the spot by a binary search over its last block
+//    and written; the others are pushed, with their state, onto the warp's
+//    ring of survivors in shared memory.  Most pixels end here, with no
+//    per-pixel bookkeeping beyond the lane they run on;
+//  * refill loop over the survivors: each lane carries two orbits; every
+//    round each orbit runs one unchecked block of kLeafUnroll updates; an
+//    orbit that escaped (or has less than a block left) parks its saved
+//    state in the warp's park buffer and its slot takes the next survivor
+//    from the ring at once (the pre-pass tops the ring up when it runs
+//    short);
 //  * when 32 orbits are parked, the warp finishes them together, one per
-//    lane: a binary search over the parked block finds the exact escape
-//    (the block's midpoint state is parked too, so the first halving costs
-//    one test; then unchecked quarter, eighth, ... blocks and one test
-//    each, the same number of steps on every lane), and the dwells are
-//    written.
+//    lane: a binary search over the parked block finds the exact escape (the
+//    block's midpoint state is parked too, so the first halving costs one
+//    test; then unchecked quarter, eighth, ... blocks and one test each, the
+//    same number of steps on every lane), and the dwells are written.
 // ---------------------------------------------------------------------------
-constexpr int kRefillWarps = 8;    // warps per CTA
-// Resident CTAs per SM: 5 for one frame (48 registers a thread; at 6 CTAs,
-// 40 registers, the refill loop spills once the fill warp's code is in the
-// kernel, and it measured slower), 4 for a batch (its per-frame lookups need
-// up to 64 registers).
-constexpr int kRefillMinBlocks = 5;
-constexpr int kRefillMinBlocksBatch = 4;
-constexpr uint32_t kParkCap = 128; // parked orbits per warp (< 32 + 2 * 32)
-constexpr int kLeafUnroll = 32;    // updates per unchecked block (a power of two)
-
-// The output and pixel mapping of the frame a leaf belongs to.
-struct LView {
-    uint32_t *map;
-    PixelMap pm;
-    uint32_t n, max_dwell;
-};
-
-template <bool BATCH>
-__device__ __forceinline__ LView leaf_view(const LeafArgs &a, uint32_t frame)
-{
-    LView v;
-    if (BATCH) {
-        const FrameDesc &d = a.frames[frame];
-        v.map = d.map;
-        v.pm = d.pm;
-        v.n = d.n;
-        v.max_dwell = d.max_dwell;
-    } else {
-        v.map = a.map;
-        v.pm = a.pm;
-        v.n = a.n;
-        v.max_dwell = a.max_dwell;
-    }
-    return v;
-}
-
-// Exact dwell of a parked orbit: s.xy = state after d updates, known to
-// pass the test, s.zw = the state kLeafUnroll / 2 updates later (the block's
-// midpoint), and "escaped, or d >= max_dwell" known to hold kLeafUnroll
-// updates later.  Points where escape is not absorbing take the tested loop
-// instead.  u = (count, py << 16 | px, frame).
-template <bool COUNT, bool BATCH>
-__device__ __forceinline__ void finish_parked(const LeafArgs &a, float4 s, uint4 u,
-                                              unsigned long long &it)
-{
-    const LView v = leaf_view<BATCH>(a, u.z);
-    const uint32_t px = u.y & 0xffffu, py = u.y >> 16;
-    const float2 c = pixel_c(v.pm, px, py);
-    uint32_t d = u.x;
-    float x = s.x, y = s.y;
-    if (!escape_absorbing(c.x, c.y)) {
-        while (d < v.max_dwell && z_bounded(x, y)) {
-            z_update(x, y, c.x, c.y);
-            ++d;
-        }
-    } else if (d < v.max_dwell) {
-        // invariant: count d passes (d < max_dwell) and the predicate holds
-        // at d + 2h; halve h until the first count where it holds is d + 1.
-        // The first halving uses the block's saved midpoint state.
-        {
-            const uint32_t h = (uint32_t)kLeafUnroll / 2u;
-            const bool hit = (v.max_dwell - d <= h) || !z_bounded(s.z, s.w);
-            if (!hit) {
-                x = s.z;
-                y = s.w;
-                d += h;
-            }
-        }
-#pragma unroll
-        for (uint32_t h = (uint32_t)kLeafUnroll / 4u; h >= 1u; h >>= 1) {
-            float tx = x, ty = y;
-#pragma unroll
-            for (uint32_t k = 0; k < h; ++k)
-                z_update(tx, ty, c.x, c.y);
-            const bool hit = (v.max_dwell - d <= h) || !z_bounded(tx, ty);
-            if (!hit) {
-                x = tx;
-                y = ty;
-                d += h;
-            }
-        }
-        d += 1u;
-    }
-    v.map[(size_t)py * v.n + px] = d;
-    if (COUNT)
-        it += d;
-}
-
-// Deferred fills ride along the leaf pass.  The last warp of every CTA
-// starts as a fill warp: it takes bands of the fill list (at most
-// kFillBandPx pixels each, 128-bit stores) from a counter until none are
-// left, then joins the leaf work; every warp that runs out of leaves helps
-// with the bands still left.  The HBM writes so proceed beside the FP32 work
-// of the other warps instead of in a kernel of their own (the bands and the
-// leaves are disjoint pixels), and the fill code sits outside the refill
-// loop, adding nothing to its registers.
-template <bool BATCH>
-__device__ __forceinline__ void drain_fills(const LeafArgs &a, uint32_t lane)
-{
-    const uint32_t nfill = min(a.ctr->fill_count, a.fill_cap);
-    for (;;) {
-        uint32_t fi = 0;
-        if (lane == 0)
-            fi = atomicAdd(&a.ctr->fill_work, 1u);
-        fi = __shfl_sync(kFull, fi, 0);
-        if (fi >= nfill)
-            return;
-        const uint4 e = a.fills[fi];
-        const Region g = unpack_region(make_uint2(e.x, e.y));
-        if (BATCH) {
-            const FrameDesc &d = a.frames[e.w];
-            fill_band_warp(d.map, d.n, g, e.z, lane);
-        } else {
-            fill_band_warp(a.map, a.n, g, e.z, lane);
-        }
-    }
-}
-
-// floor(q / w) for q < 2^22 given inv_w = 1/w rounded to float: (q + 1/2)/w
-// lies at least 1/(2w) away from an integer, far more than the rounding of
-// the two float operations, so truncation gives the exact quotient.
-__device__ __forceinline__ uint32_t rows_in(uint32_t q, float inv_w)
-{
-    return __float2uint_rz(__fmul_rz(__uint2float_rn(q) + 0.5f, inv_w));
-}
-
-// One orbit slot of a lane.
-struct Slot {
-    float x, y, cr, ci;
-    uint32_t d, pix;  // count, pixel (py << 16 | px)
-    uint32_t lim;     // a whole unchecked block may run while d < lim
-    bool busy;
-};
-
-// lim = max_dwell - kLeafUnroll + 1 where escape is absorbing (the block
-// stays within max_dwell), else 0 (such points go straight to the tested
-// loop of finish_parked).
-__device__ __forceinline__ void slot_start(Slot &o, const PixelMap &pm, uint32_t md, uint32_t px,
-                                           uint32_t py)
-{
-    const float2 c = pixel_c(pm, px, py);
-    o.cr = c.x;
-    o.ci = c.y;
-    o.x = 0.0f;
-    o.y = 0.0f;
-    o.d = 0;
-    o.pix = (py << 16) | px;
-    o.lim = (escape_absorbing(c.x, c.y) && md >= (uint32_t)kLeafUnroll) ? md - (uint32_t)kLeafUnroll + 1u
-                                                                         : 0u;
-    o.busy = true;
-}
-
-// Each lane carries two independent orbits, so one round's bookkeeping
+// The leaf kernel over the leaf list of a launch chain.  Each lane of the
+// refill loop carries two independent orbits, so one round's bookkeeping
 // (votes, refills, parking) serves two blocks of updates, and the two update
-// chains interleave.  All lanes of a warp work on the same leaf (the same
-// frame) at a time; parked orbits remember their frame.
+// chains interleave.  Parked orbits and ring entries remember their frame.
 template <bool COUNT, bool BATCH>
 __global__ void __launch_bounds__(kRefillWarps * 32, BATCH ? kRefillMinBlocksBatch : kRefillMinBlocks)
     leaf_refill_kernel(LeafArgs a)
 {
-    using R = Rec<BATCH>;
-    using T = typename R::T;
     __shared__ float4 park_s[kRefillWarps][kParkCap];  // saved state at the block's start and midpoint
     __shared__ uint4 park_u[kRefillWarps][kParkCap];   // count, pixel, frame
+    __shared__ float4 ring_s[kRefillWarps][kRingCap];  // survivor state and c
+    __shared__ uint4 ring_u[kRefillWarps][kRingCap];   // count, pixel, frame, block limit
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     if (a.fills != nullptr && wib == kRefillWarps - 1u)
         drain_fills<BATCH>(a, lane);  // the CTA's fill warp
     const unsigned lt_mask = (1u << lane) - 1u;
     float4 *qs = park_s[wib];
     uint4 *qu = park_u[wib];
-    uint32_t parked = 0;  // warp-uniform
+    float4 *rs = ring_s[wib];
+    uint4 *ru = ring_u[wib];
+    uint32_t parked = 0;             // warp-uniform
+    uint32_t ring_h = 0, ring_n = 0;  // warp-uniform: first entry, entries
 
-    const T *leaves = static_cast<const T *>(a.leaves);
-    const uint32_t nleaves = min(a.ctr->leaf_count, a.leaf_cap);
-    const uint32_t K = (uint32_t)kLeafUnroll;
-    // the warp's current leaf: the part still to hand out, as a row-major cursor
-    uint32_t rem = 0, row0 = 0, col0 = 0, ox = 0, oy = 0, cw = 1, frame = 0;
-    float inv_cw = 1.0f;
-    LView lv = leaf_view<BATCH>(a, 0u);
-    bool more = true;
+    LeafList<BATCH> src;
+    src.leaves = static_cast<const typename Rec<BATCH>::T *>(a.leaves);
+    src.nleaves = min(a.ctr->leaf_count, a.leaf_cap);
+    uint32_t srcst = SRC_MORE;
+    LeafCursor lc;
+    lc.rem = lc.row0 = lc.col0 = lc.ox = lc.oy = lc.frame = 0;
+    lc.cw = 1;
+    lc.inv_cw = 1.0f;
     Slot s0, s1;
     s0.busy = s1.busy = false;
     s0.x = s0.y = s0.cr = s0.ci = s1.x = s1.y = s1.cr = s1.ci = 0.0f;
@@ -835,130 +541,24 @@ __global__ void __launch_bounds__(kRefillWarps * 32, BATCH ? kRefillMinBlocksBat
     unsigned long long it = 0, lpx = 0;
 
     for (;;) {
-        // ---- refill idle slots: slot 0 of the idle lanes, then slot 1
-        unsigned i0 = __ballot_sync(kFull, !s0.busy), i1 = __ballot_sync(kFull, !s1.busy);
-        while ((i0 | i1) && more) {
-            if (rem == 0) {
-                uint32_t li = 0;
-                if (lane == 0)
-                    li = atomicAdd(&a.ctr->leaf_work, 1u);
-                li = __shfl_sync(kFull, li, 0);
-                if (li >= nleaves) {
-                    more = false;
-                    break;
-                }
-                const T e = leaves[li];
-                const Region g = R::region(e);
-                frame = R::frame(e);
-                if (BATCH)
-                    lv = leaf_view<BATCH>(a, frame);
-                if (a.skip_perimeter) {
-                    // only the interior; a leaf of side <= 2 is all perimeter
-                    cw = g.w > 2u ? g.w - 2u : 1u;
-                    rem = (g.w > 2u && g.h > 2u) ? (g.w - 2u) * (g.h - 2u) : 0u;
-                    ox = g.x0 + 1u;
-                    oy = g.y0 + 1u;
-                } else {
-                    cw = g.w;
-                    rem = g.w * g.h;
-                    ox = g.x0;
-                    oy = g.y0;
-                }
-                row0 = col0 = 0;
-                inv_cw = 1.0f / (float)cw;
-                continue;
-            }
-            const uint32_t n0 = (uint32_t)__popc(i0);
-            const uint32_t idle = n0 + (uint32_t)__popc(i1);
-            const uint32_t take = min(idle, rem);
-            const uint32_t r0 = (uint32_t)__popc(i0 & lt_mask);
-            const uint32_t r1 = n0 + (uint32_t)__popc(i1 & lt_mask);
-            if (!s0.busy && r0 < take) {
-                const uint32_t q = col0 + r0, dr = rows_in(q, inv_cw);
-                slot_start(s0, lv.pm, lv.max_dwell, ox + q - dr * cw, oy + row0 + dr);
-                f0 = frame;
-            }
-            if (!s1.busy && r1 < take) {
-                const uint32_t q = col0 + r1, dr = rows_in(q, inv_cw);
-                slot_start(s1, lv.pm, lv.max_dwell, ox + q - dr * cw, oy + row0 + dr);
-                f1 = frame;
-            }
-            {
-                const uint32_t q = col0 + take, dr = rows_in(q, inv_cw);
-                col0 = q - dr * cw;
-                row0 += dr;
-            }
-            rem -= take;
-            if (take == idle)
-                break;  // every slot busy
-            i0 = __ballot_sync(kFull, !s0.busy);
-            i1 = __ballot_sync(kFull, !s1.busy);
+        // refill idle slots from the ring, topping it up with pre-passes
+        // while it holds fewer survivors than idle slots (at most 32)
+        const unsigned i0 = __ballot_sync(kFull, !s0.busy), i1 = __ballot_sync(kFull, !s1.busy);
+        if (i0 | i1) {
+            const uint32_t want = min((uint32_t)(__popc(i0) + __popc(i1)), 32u);
+            while (ring_n < want && srcst == SRC_MORE)
+                pre_pass<COUNT, BATCH>(a, src, lc, srcst, rs, ru, ring_h, ring_n, lane, lt_mask, it,
+                                       lpx);
+            refill_from_ring(s0, s1, f0, f1, rs, ru, ring_h, ring_n, i0, i1, lane, lt_mask);
         }
-        // slots stay idle only once the leaves have run out
-        if (!more && !__any_sync(kFull, s0.busy || s1.busy))
+        // slots stay idle only once the leaves and the ring have run out
+        if (srcst != SRC_MORE && ring_n == 0 && !__any_sync(kFull, s0.busy || s1.busy))
             break;
-
-        // ---- one unchecked block on both slots (results of a slot that is
-        //      idle or parks this round are not used)
-        const float sx0 = s0.x, sy0 = s0.y, sx1 = s1.x, sy1 = s1.y;
-#pragma unroll
-        for (int k = 0; k < kLeafUnroll / 2; ++k) {
-            z_update(s0.x, s0.y, s0.cr, s0.ci);
-            z_update(s1.x, s1.y, s1.cr, s1.ci);
-        }
-        const float mx0 = s0.x, my0 = s0.y, mx1 = s1.x, my1 = s1.y;  // midpoint states
-#pragma unroll
-        for (int k = 0; k < kLeafUnroll / 2; ++k) {
-            z_update(s0.x, s0.y, s0.cr, s0.ci);
-            z_update(s1.x, s1.y, s1.cr, s1.ci);
-        }
-        bool park0 = false, park1 = false;
-        if (s0.busy) {
-            if (s0.d < s0.lim && z_bounded(s0.x, s0.y))
-                s0.d += K;
-            else
-                park0 = true;  // escaped in this block, tail below max_dwell, or |c| near 2
-        }
-        if (s1.busy) {
-            if (s1.d < s1.lim && z_bounded(s1.x, s1.y))
-                s1.d += K;
-            else
-                park1 = true;
-        }
-
-        // ---- park finished orbits (state before this block); finish the
-        //      top 32 parked orbits whenever there are 32
-        const unsigned p0 = __ballot_sync(kFull, park0), p1 = __ballot_sync(kFull, park1);
-        if (p0 | p1) {
-            const uint32_t n0 = (uint32_t)__popc(p0);
-            if (park0) {
-                const uint32_t slot = parked + (uint32_t)__popc(p0 & lt_mask);
-                qs[slot] = make_float4(sx0, sy0, mx0, my0);
-                qu[slot] = make_uint4(s0.d, s0.pix, f0, 0u);
-                s0.busy = false;
-            }
-            if (park1) {
-                const uint32_t slot = parked + n0 + (uint32_t)__popc(p1 & lt_mask);
-                qs[slot] = make_float4(sx1, sy1, mx1, my1);
-                qu[slot] = make_uint4(s1.d, s1.pix, f1, 0u);
-                s1.busy = false;
-            }
-            parked += n0 + (uint32_t)__popc(p1);
-            __syncwarp();
-            while (parked >= 32u) {
-                parked -= 32u;
-                const float4 sv = qs[parked + lane];
-                const uint4 uv = qu[parked + lane];
-                __syncwarp();
-                finish_parked<COUNT, BATCH>(a, sv, uv, it);
-                if (COUNT)
-                    ++lpx;
-            }
-        }
+        refill_round<COUNT, BATCH>(a, s0, s1, f0, f1, qs, qu, parked, lane, lt_mask, it, lpx);
     }
     if (a.fills != nullptr)
         drain_fills<BATCH>(a, lane);
-    // ---- the orbits still parked
+    // the orbits still parked
     if (lane < parked) {
         finish_parked<COUNT, BATCH>(a, qs[lane], qu[lane], it);
         if (COUNT)

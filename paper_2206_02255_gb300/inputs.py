@@ -69,11 +69,12 @@ def random_windows(k, seed, span=(1e-3, 3.0)):
 # ---------------------------------------------------------------------------
 # Batched and served workloads: frames zoomed on points of the set's boundary.
 # The candidate centres are boundary pixels of the n = 1024, dwell 512 map
-# (a pixel below the cap next to one at the cap), written once by
-# tests/golden/make_boundary_centers.py from the CPU reference.
+# (a pixel below the cap next to one at the cap), shipped with the package as
+# data/boundary_centers.tsv (written once from the CPU reference by
+# tests/golden/make_boundary_centers.py).
 # ---------------------------------------------------------------------------
-BOUNDARY_CENTERS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                                "tests", "golden", "boundary_centers.tsv")
+BOUNDARY_CENTERS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                                "boundary_centers.tsv")
 
 
 def boundary_centers():

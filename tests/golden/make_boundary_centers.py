@@ -1,10 +1,13 @@
-"""Write boundary_centers.tsv: seeded sample of points on the boundary of the
-n = 1024, dwell 512 map of the window [-1.5, 0.5] x [-1, 1].
+"""Write paper_2206_02255_gb300/data/boundary_centers.tsv: seeded sample of
+points on the boundary of the n = 1024, dwell 512 map of the window
+[-1.5, 0.5] x [-1, 1].
 
 A boundary pixel has a dwell below the cap and a 4-neighbour at the cap (it
 sits just outside the set, next to a pixel inside it).  The map comes from
 the CPU reference only.  The batched and served workloads take their frame
-centres from this list (see paper_2206_02255_gb300/inputs.py).
+centres from this list (see paper_2206_02255_gb300/inputs.py), which ships
+with the package as data; this script stays with the tests because it runs
+the CPU reference.
 
 Usage: python tests/golden/make_boundary_centers.py
 """
@@ -14,6 +17,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
+OUT = os.path.join(ROOT, "paper_2206_02255_gb300", "data", "boundary_centers.tsv")
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
@@ -35,7 +39,7 @@ def main():
     ys, xs = np.nonzero(~inside & nb)
     cells = sorted(zip(xs.tolist(), ys.tolist()))
     pick = random.Random(SEED).sample(cells, SAMPLE)
-    with open(os.path.join(HERE, "boundary_centers.tsv"), "w") as f:
+    with open(OUT, "w") as f:
         f.write("# %d of the %d boundary pixels of the n=%d, dwell %d map of window %s\n"
                 % (SAMPLE, len(cells), N, MAX_DWELL, WINDOW))
         f.write("# (seed %d); written by make_boundary_centers.py from the CPU reference\n" % SEED)
