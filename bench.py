@@ -33,6 +33,7 @@ METRIC = "Gpixels/s and dwell-iter/s (ASK vs exhaustive vs CDP2, 1 GB300); p50/p
 UNIT = "Gpixels/s"
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "dram_traffic_ask_n16384_d2048.json")
 KERNEL_SOURCES = ["paper_2206_02255_gb300/csrc/ask_kernels.cu",
+                  "paper_2206_02255_gb300/csrc/ask_work.cuh",
                   "paper_2206_02255_gb300/csrc/ask_device.cuh",
                   "paper_2206_02255_gb300/csrc/ask_internal.h"]
 

@@ -175,50 +175,6 @@ __device__ __forceinline__ void orbit_resolve(Orbit &o)
     o.d = d + 1u;
 }
 
-// One round of two orbits of a lane (a and b, with states sa and sb): where
-// both can take a whole unchecked block, their updates interleave (two
-// independent chains); any other orbit takes orbit_step's tested path.  The
-// outcome of each orbit is exactly orbit_step<K>'s.
-template <uint32_t K>
-__device__ __forceinline__ void orbit_step_pair(Orbit &a, uint32_t &sa, Orbit &b, uint32_t &sb,
-                                                uint32_t limit)
-{
-    const bool fa = sa == ORBIT_RUN && a.fast && a.d < limit && limit - a.d >= K;
-    const bool fb = sb == ORBIT_RUN && b.fast && b.d < limit && limit - b.d >= K;
-    if (fa || fb) {
-        float xa = a.x, ya = a.y, xb = b.x, yb = b.y;
-#pragma unroll
-        for (uint32_t k = 0; k < K; ++k) {
-            z_update(xa, ya, a.cr, a.ci);
-            z_update(xb, yb, b.cr, b.ci);
-        }
-        if (fa) {
-            if (!z_bounded(xa, ya)) {
-                sa = ORBIT_PEND;
-            } else {
-                a.x = xa;
-                a.y = ya;
-                a.d += K;
-                sa = a.d >= limit ? ORBIT_DONE : ORBIT_RUN;
-            }
-        }
-        if (fb) {
-            if (!z_bounded(xb, yb)) {
-                sb = ORBIT_PEND;
-            } else {
-                b.x = xb;
-                b.y = yb;
-                b.d += K;
-                sb = b.d >= limit ? ORBIT_DONE : ORBIT_RUN;
-            }
-        }
-    }
-    if (sa == ORBIT_RUN && !fa)
-        sa = orbit_step<K>(a, limit);
-    if (sb == ORBIT_RUN && !fb)
-        sb = orbit_step<K>(b, limit);
-}
-
 // Region record of the offset lookup tables (Sec. 5.2): origin and clipped
 // extent, 16 bits each (n <= 65536 so x0, y0, w-1, h-1 < 65536).
 struct Region {
@@ -385,64 +341,6 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
             return false;
         const uint32_t vmin = __reduce_min_sync(kLaneMask, active ? o.d : 0xffffffffu);
         const uint32_t vmax = __reduce_max_sync(kLaneMask, active ? o.d : 0u);
-        if (vmin != vmax || (have && vmin != w))
-            return false;
-        have = true;
-        w = vmin;
-    }
-    *w_out = w;
-    return true;
-}
-
-// The same query with two orbits per lane: perimeter pixels base + lane and
-// base + 32 + lane advance together, so a perimeter of up to 64 pixels is one
-// pass of lockstep rounds, and the two update chains of a lane interleave.
-// Same result and the same early stop as warp_perimeter_uniform.
-__device__ __forceinline__ bool warp_perimeter_uniform2(const PixelMap &pm, uint32_t max_dwell,
-                                                        const Region &g, uint32_t lane,
-                                                        uint32_t *w_out, unsigned long long &it)
-{
-    const uint32_t P = perimeter_size(g.w, g.h);
-    bool have = false;
-    uint32_t w = 0;
-    for (uint32_t base = 0; base < P; base += 64u) {
-        const uint32_t ka = base + lane, kb = base + 32u + lane;
-        const bool aa = ka < P, ab = kb < P;
-        const unsigned ma = __ballot_sync(kLaneMask, aa), mb = __ballot_sync(kLaneMask, ab);
-        uint32_t pxa = g.x0, pya = g.y0, pxb = g.x0, pyb = g.y0;
-        if (aa)
-            perimeter_pixel(g, ka, pxa, pya);
-        if (ab)
-            perimeter_pixel(g, kb, pxb, pyb);
-        Orbit oa = orbit_start(pixel_c(pm, pxa, pya)), ob = orbit_start(pixel_c(pm, pxb, pyb));
-        uint32_t sa = aa ? ORBIT_RUN : ORBIT_DONE, sb = ab ? ORBIT_RUN : ORBIT_DONE;
-        const uint32_t limit = have ? min(max_dwell, w + 1u) : max_dwell;
-        bool differ = false;
-        for (;;) {
-            orbit_step_pair<kQueryRound>(oa, sa, ob, sb, limit);
-            const unsigned da = __ballot_sync(kLaneMask, sa != ORBIT_RUN) & ma;
-            const unsigned db = __ballot_sync(kLaneMask, sb != ORBIT_RUN) & mb;
-            if (da == ma && db == mb)
-                break;
-            if (da | db) {
-                differ = true;
-                break;
-            }
-        }
-        if (!differ) {
-            if (sa == ORBIT_PEND)
-                orbit_resolve<kQueryRound>(oa);
-            if (sb == ORBIT_PEND)
-                orbit_resolve<kQueryRound>(ob);
-        }
-        if (aa)
-            it += oa.d;
-        if (ab)
-            it += ob.d;
-        if (differ)
-            return false;
-        const uint32_t vmin = __reduce_min_sync(kLaneMask, min(aa ? oa.d : 0xffffffffu, ab ? ob.d : 0xffffffffu));
-        const uint32_t vmax = __reduce_max_sync(kLaneMask, max(aa ? oa.d : 0u, ab ? ob.d : 0u));
         if (vmin != vmax || (have && vmin != w))
             return false;
         have = true;

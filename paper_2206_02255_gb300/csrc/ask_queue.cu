@@ -416,18 +416,32 @@ __global__ void __launch_bounds__(kRefillWarps * 32, kRefillMinBlocksBatch) queu
     bool rclosed = false;     // no region item will come any more
     uint32_t polls = 0;       // idle polls in a row
     uint32_t seen_p = 0, seen_l = 0;
-    uint32_t rounds = 0;      // leaf rounds since the ticket was last polled
+    uint32_t rounds = 0;      // leaf rounds since the held ticket's slot was loaded
+    uint32_t seen_w = 0;      // lane 0: that load (the slot's epoch word)
     bool idle = true;         // the last pass found no leaf work
 
     for (;;) {
-        // the held ticket is polled whenever the warp is idle, and every
-        // kQueuePollRounds leaf rounds while it is busy (a poll is an L2
-        // round trip the warp waits for)
-        if (!rclosed && (idle || rounds >= kQueuePollRounds)) {
-            rounds = 0;
-            if (rt == kNone)
+        // The held ticket: an idle warp polls it at once (with the check
+        // that tells a ticket past the final tail).  A busy warp loads the
+        // slot's epoch word, carries on with its leaf rounds, and reads the
+        // loaded value kQueuePollRounds rounds later, so the L2 round trip
+        // never stalls it.
+        if (!rclosed) {
+            if (rt == kNone) {
                 rt = warp_ticket(&q.qs->head, lane);
-            const int r = poll_item(q, rt, epoch, idle, lane);
+                rounds = kQueuePollRounds;  // nothing loaded yet
+                seen_w = 0;
+            }
+            int r = 0;
+            if (idle) {
+                r = poll_item(q, rt, epoch, true, lane);
+                rounds = kQueuePollRounds;
+            } else if (rounds >= kQueuePollRounds) {
+                r = __shfl_sync(kFull, seen_w == epoch ? 1 : 0, 0);
+                if (lane == 0 && rt < q.item_cap)
+                    seen_w = load_volatile(&q.items[rt].w);
+                rounds = 0;
+            }
             if (r > 0) {
                 process_item<COUNT>(q, rt, epoch, lane);
                 rt = kNone;

@@ -174,94 +174,6 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
     }
 }
 
-// chunk_query with two orbits per lane: pixels base + lane and base + 32 +
-// lane of the chunk advance together (a 64-pixel chunk is one pass of
-// lockstep rounds, the two update chains of a lane interleave).  Same
-// result, the same early stops and the same state protocol.
-template <bool BATCH>
-__device__ __forceinline__ void chunk_query2(const FView &a, const Region &g, uint32_t k0,
-                                             uint32_t k1, uint4 *st, uint32_t lane,
-                                             unsigned long long &it)
-{
-    const volatile uint32_t *ps = reinterpret_cast<const volatile uint32_t *>(st);
-    for (uint32_t base = k0; base < k1; base += 64u) {
-        uint32_t sx = 0, sy = 0;
-        if (lane == 0) {
-            sx = ps[0];
-            sy = ps[1];
-        }
-        const uint32_t ka = base + lane, kb = base + 32u + lane;
-        const bool aa = ka < k1, ab = kb < k1;
-        const unsigned ma = __ballot_sync(kFull, aa), mb = __ballot_sync(kFull, ab);
-        uint32_t pxa = g.x0, pya = g.y0, pxb = g.x0, pyb = g.y0;
-        if (aa)
-            perimeter_pixel(g, ka, pxa, pya);
-        if (ab)
-            perimeter_pixel(g, kb, pxb, pyb);
-        Orbit oa = orbit_start(pixel_c(a.pm, pxa, pya)), ob = orbit_start(pixel_c(a.pm, pxb, pyb));
-        uint32_t sa = aa ? ORBIT_RUN : ORBIT_DONE, sb = ab ? ORBIT_RUN : ORBIT_DONE;
-        bool differ = false, stop = false;
-        uint2 v = make_uint2(__shfl_sync(kFull, sx, 0), __shfl_sync(kFull, sy, 0));
-        if (v.y)
-            return;
-        uint32_t nx = v.x, ny = v.y, lag = 0;
-        for (;;) {
-            if (lag == 0 && lane == 0) {
-                nx = ps[0];
-                ny = ps[1];
-            }
-            const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
-            orbit_step_pair<kQueryRoundLarge>(oa, sa, ob, sb, limit);
-            const unsigned da = __ballot_sync(kFull, sa != ORBIT_RUN) & ma;
-            const unsigned db = __ballot_sync(kFull, sb != ORBIT_RUN) & mb;
-            if (da == ma && db == mb)
-                break;
-            if (da | db) {
-                differ = true;
-                break;
-            }
-            if (++lag == (BATCH ? 1u : kPollLag)) {
-                lag = 0;
-                v.x = __shfl_sync(kFull, nx, 0);
-                v.y = __shfl_sync(kFull, ny, 0);
-                if (v.y) {
-                    stop = true;
-                    break;
-                }
-            }
-        }
-        if (!stop && !differ) {
-            if (sa == ORBIT_PEND)
-                orbit_resolve<kQueryRoundLarge>(oa);
-            if (sb == ORBIT_PEND)
-                orbit_resolve<kQueryRoundLarge>(ob);
-        }
-        if (aa)
-            it += oa.d;
-        if (ab)
-            it += ob.d;
-        if (stop)
-            return;
-        if (differ) {
-            if (lane == 0)
-                atomicExch(&st->y, 1u);
-            return;
-        }
-        const uint32_t vmin = __reduce_min_sync(kFull, min(aa ? oa.d : kNone, ab ? ob.d : kNone));
-        const uint32_t vmax = __reduce_max_sync(kFull, max(aa ? oa.d : 0u, ab ? ob.d : 0u));
-        if (lane == 0) {
-            if (vmin != vmax) {
-                atomicExch(&st->y, 1u);
-            } else {
-                const uint32_t old = atomicCAS(&st->x, kNone, vmin);
-                if (old != kNone && old != vmin)
-                    atomicExch(&st->y, 1u);
-            }
-        }
-        __syncwarp();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Leaf machinery (see the leaf kernel in ask_kernels.cu)
 // ---------------------------------------------------------------------------
