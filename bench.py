@@ -641,7 +641,7 @@ def run_gpu(args):
         subs["large"] = measure_large(ctx, dev, local, world)
         subs["batch"] = measure_batch(ctx, dev, local, world, rank, 256, steps=1, warmup=1,
                                       probes=4, full=False)
-        subs["serve"] = measure_serve(ctx, dev, local, world, rank, sat_passes=1)
+        subs["serve"] = measure_serve(ctx, dev, local, world, rank, sat_passes=3)
 
     if rank == 0:
         line = {
@@ -873,6 +873,7 @@ def measure_serve(ctx, dev, local, world, rank, sat_passes=3, count=2000):
     # both paths share one pinned-buffer pool; results are released when
     # delivered.  Warm up (allocator caches, pinned buffers, first launches).
     pool, dpool = serve.PinnedPool(), serve.DevicePool(local)
+    pool.reserve([d["n"] for d in reqs], per_class=4)
     srv = serve.Server(device=local, slots=2, budget_bytes=40 * 2 ** 30, pool=pool, keep=False,
                        dpool=dpool)
     srv.run(fresh(reqs[:64], at_zero=True))

@@ -18,9 +18,9 @@
 //    rows), push its r x r children (Sec. 5.3.1) or append it to the leaf
 //    list;
 //  * pushes reserve slots with one atomicAdd on `tail`, write the items, and
-//    publish each by storing the render's epoch after a fence, so a slot is
-//    valid exactly when it carries the current epoch (no clearing between
-//    renders);
+//    publish each by a release store of the render's epoch (takers read it
+//    with an acquire load), so a slot is valid exactly when it carries the
+//    current epoch (no clearing between renders);
 //  * `pending` counts pushed items not yet finished; a warp that finishes an
 //    item adds (items it pushed - 1) before publishing them, so the count
 //    reaches 0 exactly when the last item is done; that warp marks the
@@ -68,6 +68,30 @@ __device__ __forceinline__ void store_volatile(uint32_t *p, uint32_t v)
     *reinterpret_cast<volatile uint32_t *>(p) = v;
 }
 
+// Acquire / release at GPU scope: a slot is published by a release store of
+// its epoch word, and taken after an acquire load of it, so its contents
+// need no full fence on either side.  Writes of other lanes of the warp are
+// ordered before a lane's release by a __syncwarp between them, and reads of
+// other lanes after a lane's acquire the same way.
+__device__ __forceinline__ uint32_t load_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t *p, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // A ticket of the warp: lane 0 takes it, every lane gets it.
 __device__ __forceinline__ uint32_t warp_ticket(uint32_t *counter, uint32_t lane)
 {
@@ -78,16 +102,13 @@ __device__ __forceinline__ uint32_t warp_ticket(uint32_t *counter, uint32_t lane
 }
 
 // Finish an item that pushed nothing: the warp's earlier writes first, then
-// the count; the warp that takes it to 0 marks the render's regions done.
+// the count (an acquire-release add, so the counts form one chain of
+// releases); the warp that takes it to 0 marks the render's regions done.
 __device__ __forceinline__ void finish_item(const QueueArgs &q, uint32_t epoch, uint32_t lane)
 {
-    if (lane == 0) {
-        __threadfence();
-        if (atomicAdd(&q.qs->pending, 0xffffffffu) == 1u) {
-            __threadfence();
-            store_volatile(&q.qs->done, epoch);
-        }
-    }
+    __syncwarp();
+    if (lane == 0 && atomic_add_acq_rel(&q.qs->pending, 0xffffffffu) == 1u)
+        store_release(&q.qs->done, epoch);
     __syncwarp();
 }
 
@@ -108,20 +129,16 @@ __device__ __forceinline__ uint32_t reserve_items(const QueueArgs &q, uint32_t n
 
 // Publish the n items written at base (each lane its own, written by it):
 // the count of pending items first grows by n - 1 (the finishing item
-// replaced by its n), then each item gets the epoch after a fence.
+// replaced by its n), then each item gets the epoch by a release store.
 __device__ __forceinline__ void publish_items(const QueueArgs &q, uint32_t base, uint32_t n,
                                               uint32_t epoch, uint32_t lane)
 {
-    __threadfence();
     __syncwarp();
-    if (lane == 0) {
-        atomicAdd(&q.qs->pending, n - 1u);
-        __threadfence();
-    }
+    if (lane == 0)
+        atomic_add_acq_rel(&q.qs->pending, n - 1u);
     __syncwarp();
-    __threadfence();
     for (uint32_t k = lane; k < n; k += 32u)
-        store_volatile(&q.items[base + k].w, epoch);
+        store_release(&q.items[base + k].w, epoch);
     __syncwarp();
 }
 
@@ -133,11 +150,10 @@ __device__ __forceinline__ int poll_item(const QueueArgs &q, uint32_t t, uint32_
 {
     int r = 0;
     if (lane == 0) {
-        if (t < q.item_cap && load_volatile(&q.items[t].w) == epoch) {
+        if (t < q.item_cap && load_acquire(&q.items[t].w) == epoch) {
             r = 1;
-        } else if (final && load_volatile(&q.qs->done) == epoch) {
-            __threadfence();
-            r = (t < q.item_cap && load_volatile(&q.items[t].w) == epoch) ? 1 : -1;
+        } else if (final && load_acquire(&q.qs->done) == epoch) {
+            r = (t < q.item_cap && load_acquire(&q.items[t].w) == epoch) ? 1 : -1;
         }
     }
     return __shfl_sync(kFull, r, 0);
@@ -157,13 +173,15 @@ struct QueueLeaves {
             ticket = warp_ticket(&q->qs->leaf_head, lane);
         const uint32_t t = ticket;
         int r = 0;
+        uint4 e = make_uint4(0u, 0u, 0u, 0u);
         if (lane == 0) {
-            if (t < q->leaf_cap && load_volatile(&q->leaves[t].w) == epoch) {
+            if (t < q->leaf_cap && load_acquire(&q->leaves[t].w) == epoch) {
                 r = 1;
-            } else if (load_volatile(&q->qs->done) == epoch) {
-                __threadfence();
-                r = (t < q->leaf_cap && load_volatile(&q->leaves[t].w) == epoch) ? 1 : -1;
+            } else if (load_acquire(&q->qs->done) == epoch) {
+                r = (t < q->leaf_cap && load_acquire(&q->leaves[t].w) == epoch) ? 1 : -1;
             }
+            if (r > 0)
+                e = __ldcg(&q->leaves[t]);  // after the acquire
         }
         r = __shfl_sync(kFull, r, 0);
         if (r == 0)
@@ -171,8 +189,9 @@ struct QueueLeaves {
         ticket = kNone;
         if (r < 0)
             return SRC_DONE;
-        __threadfence();
-        const uint4 e = __ldcg(&q->leaves[t]);
+        e.x = __shfl_sync(kFull, e.x, 0);
+        e.y = __shfl_sync(kFull, e.y, 0);
+        e.z = __shfl_sync(kFull, e.z, 0);
         cursor_at(lc, unpack_region(make_uint2(e.x, e.y)), e.z, false);
         return SRC_MORE;
     }
@@ -184,9 +203,19 @@ template <bool COUNT>
 __device__ __forceinline__ void process_item(const QueueArgs &q, uint32_t t, uint32_t epoch,
                                              uint32_t lane)
 {
-    __threadfence();
-    const uint4 e = __ldcg(&q.items[t]);
-    const uint32_t aux = __ldcg(&q.aux[t]);
+    // lane 0 takes the slot (an acquire of its epoch word, which the poll
+    // saw published) and hands its contents to the warp
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t aux = 0;
+    if (lane == 0) {
+        (void)load_acquire(&q.items[t].w);
+        e = __ldcg(&q.items[t]);
+        aux = __ldcg(&q.aux[t]);
+    }
+    e.x = __shfl_sync(kFull, e.x, 0);
+    e.y = __shfl_sync(kFull, e.y, 0);
+    e.z = __shfl_sync(kFull, e.z, 0);
+    aux = __shfl_sync(kFull, aux, 0);
     const uint32_t frame = e.z & 0xfffffu, level = (e.z >> 20) & 31u;
     const uint32_t kind = (e.z >> 25) & 1u, c = e.z >> 26;
     const Region g = unpack_region(make_uint2(e.x, e.y));
@@ -213,12 +242,8 @@ __device__ __forceinline__ void process_item(const QueueArgs &q, uint32_t t, uin
             chunk_query<true>(f, g, k0, k1, st, lane, it);
         // the warp that finishes the region's last chunk decides
         uint32_t last = 0;
-        if (lane == 0) {
-            __threadfence();
-            last = (atomicAdd(&st->z, 1u) == C - 1u) ? 1u : 0u;
-            if (last)
-                __threadfence();
-        }
+        if (lane == 0)
+            last = (atomic_add_acq_rel(&st->z, 1u) == C - 1u) ? 1u : 0u;
         last = __shfl_sync(kFull, last, 0);
         if (last) {
             uint32_t sx = 0, sy = 0;
@@ -280,8 +305,7 @@ __device__ __forceinline__ void process_item(const QueueArgs &q, uint32_t t, uin
                 l->x = e.x;
                 l->y = e.y;
                 l->z = frame;
-                __threadfence();
-                store_volatile(&l->w, epoch);
+                store_release(&l->w, epoch);
             } else {
                 atomicOr(&q.ctr->error, ERR_LEAF_OVERFLOW);
             }

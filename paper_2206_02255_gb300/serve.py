@@ -15,10 +15,11 @@ Requests that arrive
 while batches run wait for the next free slot.  A request's latency runs
 from its arrival to the moment its map is in host memory.
 
-Batching pays only when requests queue up.  A slot that admits a single
-request dispatches it through the single-frame call (no frame table to
-build and copy), so a lightly loaded server adds nothing to the per-frame
-path.  While work is in flight the server polls its events without
+Batching pays only when requests queue up.  A slot admits a batch only
+when at least ``batch_min`` requests wait; otherwise it takes one request
+and dispatches it through the single-frame call (no frame table to build
+and copy), its map copied right behind its render, so a lightly loaded
+server adds nothing to the per-frame path.  While work is in flight the server polls its events without
 sleeping; it sleeps only when it is idle until the next arrival.
 
 Requests zoomed past ``ask.FP64_ZOOM`` are rendered in double precision
@@ -68,6 +69,19 @@ class PinnedPool:
 
     def put(self, buf):
         self.free.setdefault(buf.numel(), []).append(buf)
+
+    def reserve(self, sides, per_class=2):
+        """Carve `per_class` buffers of every size class that maps of the
+        given sides need, so that serving them allocates no slab (pinning
+        1 GiB takes about 75 ms)."""
+        need = {}
+        for n in sides:
+            cls = 1 << max(12, (4 * n * n - 1).bit_length())
+            need[cls] = per_class
+        for cls, k in sorted(need.items()):
+            have = len(self.free.get(cls, []))
+            for _ in range(max(0, k - have)):
+                self.put(self._carve(cls))
 
 
 class DevicePool:
@@ -126,7 +140,7 @@ class Server:
     """Continuous-batching server over `slots` contexts on one device."""
 
     def __init__(self, device=0, slots=2, budget_bytes=40 * 2 ** 30, max_frames=256, pool=None,
-                 keep=True, dpool=None):
+                 keep=True, dpool=None, batch_min=4):
         import torch
         self.device = device
         self.pool = pool if pool is not None else PinnedPool()
@@ -134,6 +148,10 @@ class Server:
         self.keep = keep  # keep results on the requests; else recycle at completion
         self.budget = budget_bytes
         self.max_frames = max_frames
+        # a slot batches only when at least batch_min requests wait; with
+        # fewer, it takes one through the single-frame call (a short burst
+        # renders faster as single frames back to back than as a batch)
+        self.batch_min = batch_min
         self.ctxs = [ask.Context(device) for _ in range(slots)]
         self.compute = torch.cuda.Stream(device=device)
         self.copy = torch.cuda.Stream(device=device)  # the copies of every slot
@@ -166,14 +184,22 @@ class Server:
                     if ask.needs_fp64(q.window):
                         render_one(self.ctxs[slot], q, c)
                 self.batch_dispatches += 1
-            rendered = torch.cuda.Event()
-            rendered.record(c)
-        s.wait_event(rendered)
-        with torch.cuda.stream(s):
-            for q in reqs:
-                q.host.copy_(q.out, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
+            if len(reqs) == 1:
+                # a lone request's map is copied right behind its render on
+                # the compute stream, as the per-frame path does
+                reqs[0].host.copy_(reqs[0].out, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(c)
+            else:
+                rendered = torch.cuda.Event()
+                rendered.record(c)
+        if len(reqs) > 1:
+            s.wait_event(rendered)
+            with torch.cuda.stream(s):
+                for q in reqs:
+                    q.host.copy_(q.out, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s)
         for q in reqs:
             q.event = ev
         self.busy[slot] = reqs
@@ -212,7 +238,8 @@ class Server:
                 if self.busy[slot] is not None or not pending:
                     continue
                 take, mem = [], 0
-                while pending and len(take) < self.max_frames and \
+                limit = self.max_frames if len(pending) >= self.batch_min else 1
+                while pending and len(take) < limit and \
                         self.used + mem + pending[0].nbytes <= self.budget:
                     mem += pending[0].nbytes
                     take.append(pending.pop(0))
