@@ -416,12 +416,29 @@ __device__ __forceinline__ uint32_t pre_pass(const LeafArgs &a, Src &src, LeafCu
     const uint32_t px = pix & 0xffffu, py = pix >> 16;
     const float2 c = pixel_c(v.pm, px, py);
     const bool absorbing = escape_absorbing(c.x, c.y);
-    float x = 0.0f, y = 0.0f;
+    // A lane runs while its orbit passes every block's test; (ex, ey) keeps
+    // the state a stopped lane stopped at (the start of its escaping block,
+    // or, in a batch, the state its own max_dwell left no room beyond), so
+    // a stopped lane's (x, y) may run on to garbage with no rollback.  d
+    // counts only the blocks a lane ran.
+    float x = 0.0f, y = 0.0f, ex = 0.0f, ey = 0.0f;
     uint32_t d = 0;
     bool run = have && absorbing, esc = false;
+    // one frame: the blocks that fit below max_dwell, the same for every lane
+    const uint32_t nb = BATCH ? (uint32_t)(kPrePass / kPreBlock)
+                              : min((uint32_t)(kPrePass / kPreBlock), v.max_dwell / (uint32_t)kPreBlock);
 #pragma unroll
     for (int b = 0; b < kPrePass / kPreBlock; ++b) {
-        run = run && (v.max_dwell - d >= (uint32_t)kPreBlock);  // a whole block fits
+        if (!BATCH && (uint32_t)b >= nb)
+            break;
+        if (BATCH) {
+            const bool fits = v.max_dwell - d >= (uint32_t)kPreBlock;  // a whole block fits
+            if (run && !fits) {
+                ex = x;
+                ey = y;
+            }
+            run = run && fits;
+        }
         if (!__any_sync(kFull, run))
             break;
         const float sx = x, sy = y;
@@ -429,20 +446,23 @@ __device__ __forceinline__ uint32_t pre_pass(const LeafArgs &a, Src &src, LeafCu
         for (int k = 0; k < kPreBlock; ++k)
             z_update(x, y, c.x, c.y);
         const bool ok = z_bounded(x, y);
-        if (run && !ok)
+        if (run && !ok) {
             esc = true;  // the dwell lies in (d, d + kPreBlock]
-        if (run && ok) {
-            d += (uint32_t)kPreBlock;
-        } else {
-            x = sx;
-            y = sy;
+            ex = sx;
+            ey = sy;
         }
+        if (run && ok)
+            d += (uint32_t)kPreBlock;
         run = run && ok;
+    }
+    if (run) {
+        ex = x;
+        ey = y;
     }
     if (__any_sync(kFull, esc)) {
         // invariant: the state at count d passes the test and the state at
         // d + 2h fails; halve h until the first failing count is d + 1
-        float rx = x, ry = y;
+        float rx = ex, ry = ey;
         uint32_t rd = d;
 #pragma unroll
         for (uint32_t h = (uint32_t)kPreBlock / 2u; h >= 1u; h >>= 1) {
@@ -472,7 +492,7 @@ __device__ __forceinline__ uint32_t pre_pass(const LeafArgs &a, Src &src, LeafCu
             slot -= kRingCap;
         const uint32_t K = (uint32_t)kLeafUnroll;
         const uint32_t lim = (absorbing && v.max_dwell >= K) ? v.max_dwell - K + 1u : 0u;
-        rs[slot] = make_float4(x, y, c.x, c.y);
+        rs[slot] = make_float4(ex, ey, c.x, c.y);
         ru[slot] = make_uint4(d, pix, frame, lim);
     }
     ring_n += (uint32_t)__popc(pm);
