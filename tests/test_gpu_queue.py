@@ -64,6 +64,25 @@ def test_persistent_batch_matches_oracle(ctx, orc, asklib):
     assert st["leaves"] == leaves
 
 
+def test_persistent_batch_tiny_and_ragged_frames(ctx, orc, asklib):
+    """Frames of 1 to 64 pixels a side under every (g, r, B) in a small set,
+    one persistent batch: regions of side 1 and 2, clipped children, a
+    single initial region, leaves at the first level."""
+    import itertools
+    import torch
+    specs = []
+    for n, (g, r, B) in itertools.product((1, 2, 3, 5, 8, 16, 64),
+                                          itertools.product((1, 2, 3), (2, 3), (1, 2, 4))):
+        if g <= n:
+            specs.append((inputs.WINDOW_WIDE if n % 2 else inputs.WINDOW_PAPER, n, 50 + n, g, r, B))
+    frames = _frames(specs)
+    ctx.render_batch(frames, flags=asklib.FLAG_PERSISTENT)
+    torch.cuda.synchronize()
+    for f, (win, n, M, g, r, B) in zip(frames, specs):
+        want, _ = orc.render_ms(win, n, M, g, r, B)
+        assert np.array_equal(_map(f["out"]), want), (n, g, r, B)
+
+
 def test_persistent_batch_twice_and_after_the_chain(ctx, orc, asklib):
     """Renders in a row on one context (each render's queue slots carry a new
     epoch, so the previous render's items are never taken for this one's),

@@ -36,6 +36,7 @@ def test_served_results_equal_oracle_and_alone(ctx, orc, asklib):
     srv.run(rs)
     srv.close()
     assert peak[0] <= budget
+    assert srv.batch_dispatches >= 1  # requests queued up: the batch path ran
     base = [serve.Request(d, *params[d["id"] % 3]) for d in reqs]
     serve.serve_per_frame(ctx, base)
     for q, b in zip(rs, base):
