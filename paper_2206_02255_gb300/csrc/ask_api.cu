@@ -573,7 +573,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
                 stats->fills_per_level[i] = c.fills[i];
                 stats->subdivisions_per_level[i] = c.subdivs[i];
             }
-            stats->leaves = c.leaf_count;
+            stats->leaves = c.leaf_count + c.leaf_light;
             stats->iterations = c.iterations;
             stats->kernel_launches = launches;
         }
@@ -701,7 +701,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
             stats->subdivisions_per_level[i] = c.subdivs[i];
             stats->iterations_per_level[i] = c.level_iters[i];
         }
-        stats->leaves = c.leaf_count;
+        stats->leaves = c.leaf_count + c.leaf_light;
         stats->fill_pixels = c.fill_pixels;
         stats->deferred_fill_pixels = c.deferred_fill_pixels;
         stats->leaf_pixels = c.leaf_pixels;
@@ -1386,7 +1386,7 @@ ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nfra
             stats->subdivisions_per_level[i] = c.subdivs[i];
             stats->iterations_per_level[i] = c.level_iters[i];
         }
-        stats->leaves = c.leaf_count;
+        stats->leaves = c.leaf_count + c.leaf_light;
         stats->fill_pixels = c.fill_pixels;
         stats->deferred_fill_pixels = c.deferred_fill_pixels;
         stats->leaf_pixels = c.leaf_pixels;
@@ -1637,7 +1637,7 @@ ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *wi
             stats->subdivisions_per_level[i] = c.subdivs[i];
             stats->iterations_per_level[i] = c.level_iters[i];
         }
-        stats->leaves = c.leaf_count;
+        stats->leaves = c.leaf_count + c.leaf_light;
         stats->fill_pixels = c.fill_pixels;
         stats->leaf_pixels = c.leaf_pixels;
         stats->iterations = c.iterations;

@@ -20,7 +20,8 @@ struct DevCounters {
     uint32_t count[ASK_MAX_LEVELS + 1];     // entries in the region table of level i
     uint32_t fills[ASK_MAX_LEVELS];         // uniform regions filled at level i
     uint32_t subdivs[ASK_MAX_LEVELS];       // regions split at level i
-    uint32_t leaf_count;                    // entries in the leaf list
+    uint32_t leaf_count;                    // leaf-list entries from the front (all of them,
+                                            // where the producer does not order its leaves)
     uint32_t error;                         // ERR_* bits, latched
     unsigned long long iterations;          // COUNT mode: z-updates
     unsigned long long fill_pixels;         // COUNT mode
@@ -33,7 +34,8 @@ struct DevCounters {
     uint32_t leaf_work;                     // next leaf the leaf kernel hands out
     uint32_t fill_count;                    // bands in the deferred-fill list
     uint32_t fill_work;                     // next band the leaf kernel's fill warps take
-    uint32_t pad_;
+    uint32_t leaf_light;                    // leaf-list entries from the back (level kernels:
+                                            // leaves whose probe escaped, taken last)
 };
 
 enum : uint32_t {

@@ -349,12 +349,34 @@ __device__ __forceinline__ void cursor_at(LeafCursor &lc, const Region &g, uint3
     lc.inv_cw = 1.0f / (float)lc.cw;
 }
 
+// A leaf list is filled from both ends: leaf_count entries from the front
+// (the leaves likely to hold long orbits, or every leaf where the producer
+// does not order them) and leaf_light from the back.  Leaf t of the order in
+// which they are taken (the front first, then the back in append order) sits
+// at this slot.
+__device__ __forceinline__ uint32_t leaf_slot(uint32_t t, uint32_t front, uint32_t cap)
+{
+    return t < front ? t : cap - 1u - (t - front);
+}
+
+// Entries of the front and of the whole list, within `cap`.  More leaves
+// than `cap` (front and back met) latch the overflow error; block 0 reports.
+__device__ __forceinline__ void leaf_extent(DevCounters *ctr, uint32_t cap, uint32_t &front,
+                                            uint32_t &total)
+{
+    const uint32_t h = ctr->leaf_count, l = ctr->leaf_light;
+    front = min(h, cap);
+    total = front + min(l, cap - front);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (unsigned long long)h + l > cap)
+        atomicOr(&ctr->error, ERR_LEAF_OVERFLOW);
+}
+
 // The leaf list of a launch chain: complete when the leaf kernel starts, its
 // leaves handed out one at a time by a device counter.
 template <bool BATCH>
 struct LeafList {
     const typename Rec<BATCH>::T *leaves;
-    uint32_t nleaves;
+    uint32_t front, total, cap;
 
     __device__ __forceinline__ uint32_t next(const LeafArgs &a, LeafCursor &lc, uint32_t lane)
     {
@@ -363,9 +385,9 @@ struct LeafList {
         if (lane == 0)
             li = atomicAdd(&a.ctr->leaf_work, 1u);
         li = __shfl_sync(kFull, li, 0);
-        if (li >= nleaves)
+        if (li >= total)
             return SRC_DONE;
-        const typename R::T e = leaves[li];
+        const typename R::T e = leaves[leaf_slot(li, front, cap)];
         cursor_at(lc, R::region(e), R::frame(e), a.skip_perimeter != 0u);
         return SRC_MORE;
     }
