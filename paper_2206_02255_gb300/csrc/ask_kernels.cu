@@ -588,11 +588,19 @@ __global__ void __launch_bounds__(kRefillWarps * 32, BATCH ? kRefillMinBlocksBat
                                        lpx);
             refill_from_ring(s0, s1, f0, f1, rs, ru, ring_h, ring_n, i0, i1, lane, lt_mask);
         }
-        // slots stay idle only once the leaves and the ring have run out
-        if (srcst != SRC_MORE && ring_n == 0 && !__any_sync(kFull, s0.busy || s1.busy))
+        // once the leaves have run out and the orbits left fit in one slot
+        // per lane, the tail runs on slot 0 alone
+        if (srcst != SRC_MORE &&
+            ring_n + (uint32_t)__popc(__ballot_sync(kFull, s0.busy)) +
+                    (uint32_t)__popc(__ballot_sync(kFull, s1.busy)) <= 32u)
             break;
         refill_round<COUNT, BATCH>(a, s0, s1, f0, f1, qs, qu, parked, lane, lt_mask, it, lpx);
     }
+    fold_slot1(s1, f1, rs, ru, ring_h, ring_n, lt_mask);
+    refill_from_ring(s0, s1, f0, f1, rs, ru, ring_h, ring_n, __ballot_sync(kFull, !s0.busy), 0u, lane,
+                     lt_mask);
+    while (__any_sync(kFull, s0.busy))
+        refill_round<COUNT, BATCH, false>(a, s0, s1, f0, f1, qs, qu, parked, lane, lt_mask, it, lpx);
     if (a.fills != nullptr)
         drain_fills<BATCH>(a, lane);
     // the orbits still parked

@@ -573,13 +573,34 @@ __device__ __forceinline__ void refill_from_ring(Slot &s0, Slot &s1, uint32_t &f
     __syncwarp();
 }
 
+// Move the orbits of slot 1 onto the ring (the ring and both slots hold at
+// most 32 orbits between them when this is called), so the refill that
+// follows puts every orbit in slot 0 and the rounds after it update one
+// orbit per lane: once the leaves have run out and few orbits are left, a
+// round then costs half the instructions.
+__device__ __forceinline__ void fold_slot1(Slot &s1, uint32_t f1, float4 *rs, uint4 *ru,
+                                           uint32_t ring_h, uint32_t &ring_n, unsigned lt_mask)
+{
+    const unsigned b1 = __ballot_sync(kFull, s1.busy);
+    if (s1.busy) {
+        uint32_t slot = ring_h + ring_n + (uint32_t)__popc(b1 & lt_mask);
+        if (slot >= kRingCap)
+            slot -= kRingCap;
+        rs[slot] = make_float4(s1.x, s1.y, s1.cr, s1.ci);
+        ru[slot] = make_uint4(s1.d, s1.pix, f1, s1.lim);
+        s1.busy = false;
+    }
+    ring_n += (uint32_t)__popc(b1);
+    __syncwarp();
+}
+
 // One round of the refill loop: an unchecked block of kLeafUnroll updates on
-// both slots (the results of a slot that is idle or parks are not used); an
-// orbit that escaped in the block, has less than a block left below
-// max_dwell or has |c| near 2 parks its state before the block (and the
-// block's midpoint state) in the park buffer; whenever 32 orbits are parked
-// the warp finishes them together.
-template <bool COUNT, bool BATCH>
+// both slots (TWO) or on slot 0 alone (the results of a slot that is idle or
+// parks are not used); an orbit that escaped in the block, has less than a
+// block left below max_dwell or has |c| near 2 parks its state before the
+// block (and the block's midpoint state) in the park buffer; whenever 32
+// orbits are parked the warp finishes them together.
+template <bool COUNT, bool BATCH, bool TWO = true>
 __device__ __forceinline__ void refill_round(const LeafArgs &a, Slot &s0, Slot &s1, uint32_t f0,
                                              uint32_t f1, float4 *qs, uint4 *qu, uint32_t &parked,
                                              uint32_t lane, unsigned lt_mask, unsigned long long &it,
@@ -590,13 +611,15 @@ __device__ __forceinline__ void refill_round(const LeafArgs &a, Slot &s0, Slot &
 #pragma unroll
     for (int k = 0; k < kLeafUnroll / 2; ++k) {
         z_update(s0.x, s0.y, s0.cr, s0.ci);
-        z_update(s1.x, s1.y, s1.cr, s1.ci);
+        if (TWO)
+            z_update(s1.x, s1.y, s1.cr, s1.ci);
     }
     const float mx0 = s0.x, my0 = s0.y, mx1 = s1.x, my1 = s1.y;  // midpoint states
 #pragma unroll
     for (int k = 0; k < kLeafUnroll / 2; ++k) {
         z_update(s0.x, s0.y, s0.cr, s0.ci);
-        z_update(s1.x, s1.y, s1.cr, s1.ci);
+        if (TWO)
+            z_update(s1.x, s1.y, s1.cr, s1.ci);
     }
     bool park0 = false, park1 = false;
     if (s0.busy) {
@@ -605,7 +628,7 @@ __device__ __forceinline__ void refill_round(const LeafArgs &a, Slot &s0, Slot &
         else
             park0 = true;
     }
-    if (s1.busy) {
+    if (TWO && s1.busy) {
         if (s1.d < s1.lim && z_bounded(s1.x, s1.y))
             s1.d += K;
         else
