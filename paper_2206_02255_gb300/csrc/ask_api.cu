@@ -600,10 +600,17 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
     mk.at(0, s);
     if (row0 >= plan.axis0)
         return set_err(ctx, ASK_EINVAL, "band starts past the last initial-region row");
+    const uint32_t rows0 = std::min(rows, plan.axis0 - row0);
     if ((e = launch_init(ctx->olt[0], plan.chunks[0] > 1u ? ctx->rst[0] : nullptr, ctx->ctr, n,
-                         plan.side[0], plan.axis0, row0, std::min(rows, plan.axis0 - row0), s)) !=
+                         plan.side[0], plan.axis0, row0, rows0, s, (sbr || mbr) ? nullptr : &pm)) !=
         cudaSuccess)
         return cuda_err(ctx, e, "init kernel");
+    // the bound on level i's regions, which its table fills from both ends:
+    // the initial regions written, then (intervals per axis)^2
+    auto level_cap = [&](uint32_t i) -> uint32_t {
+        const uint64_t c = (i == 0) ? (uint64_t)plan.axis0 * rows0 : plan.max_regions[i];
+        return (uint32_t)std::min<uint64_t>(c, olt_cap);
+    };
     ++launches;
     mk.at(1, s);
     for (uint32_t i = 0; i < L; ++i) {
@@ -620,6 +627,8 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.olt_in = ctx->olt[i & 1];
         a.olt_out = ctx->olt[(i + 1) & 1];
         a.olt_cap = olt_cap;
+        a.in_cap = level_cap(i);
+        a.out_cap = (i + 1 < L) ? level_cap(i + 1) : 0u;
         a.chunks = plan.chunks[i];
         a.next_chunks = (i + 1 < L) ? plan.chunks[i + 1] : 1u;
         a.rst_in = ctx->rst[i & 1];
@@ -696,7 +705,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         const DevCounters &c = *ctx->h_ctr;
         stats->levels = L;
         for (uint32_t i = 0; i < L; ++i) {
-            stats->regions_per_level[i] = c.count[i];
+            stats->regions_per_level[i] = c.count[i] + c.back[i];
             stats->fills_per_level[i] = c.fills[i];
             stats->subdivisions_per_level[i] = c.subdivs[i];
             stats->iterations_per_level[i] = c.level_iters[i];
@@ -721,6 +730,7 @@ struct BatchPlan {
     uint32_t L = 0;                       // deepest level over the frames
     uint32_t chunks[ASK_MAX_LEVELS] = {};  // chunks per region at each level (max over frames)
     uint64_t olt_need = 0, leaf_need = 0, rst_need = 0, fill_need = 0;
+    uint64_t level_cap[ASK_MAX_LEVELS] = {};  // bound on each level's regions over the frames
     uint32_t total0 = 0;
     // the persistent batch kernel: queue items (every level's chunk items and
     // fill bands of every frame), chunk states, level-0 items and states
@@ -807,6 +817,7 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
         bp.chunks[i] = std::min(bp.chunks[i], kMaxChunksBatch);
         if (level_regions[i] * bp.chunks[i] >= 0xffffffffull)
             return set_err(ctx, ASK_EINVAL, "batch too large: level %u holds too many work items", i);
+        bp.level_cap[i] = level_regions[i];
         if (level_regions[i] > bp.olt_need)
             bp.olt_need = level_regions[i];
         if (bp.chunks[i] > 1u && level_regions[i] > bp.rst_need)
@@ -897,6 +908,8 @@ ask_status enqueue_batch(ask_ctx *ctx, const BatchBuffers &b, const BatchPlan &b
         a.olt_in = b.olt[i & 1];
         a.olt_out = b.olt[(i + 1) & 1];
         a.olt_cap = (uint32_t)b.olt_cap;
+        a.in_cap = (i == 0) ? bp.total0 : (uint32_t)bp.level_cap[i];
+        a.out_cap = (i + 1 < bp.L) ? (uint32_t)bp.level_cap[i + 1] : 0u;
         a.chunks = bp.chunks[i];
         a.next_chunks = (i + 1 < bp.L) ? bp.chunks[i + 1] : 1u;
         a.rst_in = b.rst[i & 1];
@@ -1381,7 +1394,7 @@ ask_status ask_render_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nfra
         const DevCounters &c = *ctx->h_ctr;
         stats->levels = bp.L;
         for (uint32_t i = 0; i < bp.L; ++i) {
-            stats->regions_per_level[i] = c.count[i];
+            stats->regions_per_level[i] = c.count[i] + c.back[i];
             stats->fills_per_level[i] = c.fills[i];
             stats->subdivisions_per_level[i] = c.subdivs[i];
             stats->iterations_per_level[i] = c.level_iters[i];
@@ -1632,7 +1645,7 @@ ask_status render64_impl(ask_ctx *ctx, ask_method method, const ask_window64 *wi
         const DevCounters &c = *ctx->h_ctr;
         stats->levels = L;
         for (uint32_t i = 0; i < L; ++i) {
-            stats->regions_per_level[i] = c.count[i];
+            stats->regions_per_level[i] = c.count[i] + c.back[i];
             stats->fills_per_level[i] = c.fills[i];
             stats->subdivisions_per_level[i] = c.subdivs[i];
             stats->iterations_per_level[i] = c.level_iters[i];

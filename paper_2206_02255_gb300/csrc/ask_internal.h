@@ -36,6 +36,8 @@ struct DevCounters {
     uint32_t fill_work;                     // next band the leaf kernel's fill warps take
     uint32_t leaf_light;                    // leaf-list entries from the back (level kernels:
                                             // leaves whose probe escaped, taken last)
+    uint32_t back[ASK_MAX_LEVELS + 1];      // region-table entries of level i written from the
+                                            // back (count[i] holds those from the front)
 };
 
 enum : uint32_t {
@@ -74,9 +76,15 @@ cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t m
                               cudaStream_t s);
 // Zero the counters (except the latched error word) and, if olt0 is set,
 // write the initial regions of initial-region rows [row0, row0 + rows) of the
-// axis0 x axis0 grid of side s0 (count[0] = axis0 * rows).
+// axis0 x axis0 grid of side s0 (count[0] = axis0 * rows).  With `order`
+// (the frame's pixel map) and at most kInitOrderMax regions, the regions
+// whose centre orbit stays bounded for a probe's updates fill the table from
+// the front (count[0]) and the others from the back (back[0]), so the level
+// kernel takes the long ones first.
+constexpr uint32_t kInitOrderMax = 4096;
 cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
-                        uint32_t axis0, uint32_t row0, uint32_t rows, cudaStream_t s);
+                        uint32_t axis0, uint32_t row0, uint32_t rows, cudaStream_t s,
+                        const PixelMap *order = nullptr);
 
 // One frame of a batch, resident on the device.  Region records of a batch
 // are uint4 {x0 | y0 << 16, (w-1) | (h-1) << 16, frame, 0}.
@@ -109,6 +117,10 @@ struct LevelArgs {
     const void *olt_in;   // uint2 records (single frame) or uint4 records (batch)
     void *olt_out;
     uint32_t olt_cap;     // capacity of both region tables
+    uint32_t in_cap;      // bound on this level's regions (<= olt_cap): olt_in holds
+                          //   count[level] entries from slot 0 up and back[level] from
+                          //   slot in_cap - 1 down
+    uint32_t out_cap;     // the same bound for the next level's table (olt_out, rst_out)
     uint32_t chunks;      // perimeter chunks per region at this level (1 = one warp per region)
     uint32_t next_chunks; // chunks per region at the next level
     uint4 *rst_in;        // per-region query state of this level (chunks > 1)

@@ -75,12 +75,37 @@ __global__ void __launch_bounds__(1024) exhaustive_kernel(uint32_t *__restrict__
     }
 }
 
+// Order probe of a region (the order in which the region tables and the
+// leaf list are taken): does the orbit of the region's centre pixel stay
+// bounded for kLeafProbe updates?  Regions inside the set, whose perimeter
+// orbits all run to max_dwell, and leaves holding such orbits answer yes;
+// taking them first lets a kernel's warps run out of work together instead
+// of ending on a wave of its longest items.  Only the order of the work
+// depends on it, never a dwell.  Unchecked updates: an escaped orbit runs to
+// inf or NaN and fails the test; where escape is not absorbing the answer is
+// no.
+__device__ __forceinline__ bool region_probe(const PixelMap &pm, const Region &g)
+{
+    const float2 c = pixel_c(pm, g.x0 + g.w / 2u, g.y0 + g.h / 2u);
+    if (!escape_absorbing(c.x, c.y))
+        return false;
+    float x = 0.0f, y = 0.0f;
+#pragma unroll 8
+    for (int k = 0; k < kLeafProbe; ++k)
+        z_update(x, y, c.x, c.y);
+    return z_bounded(x, y);
+}
+
 // Zero the per-render counters (the latched error word is kept), write the
 // level-0 OLT (the axis0 x axis0 non-empty initial regions of side s0) and,
-// when level 0 is queried in chunks, its per-region state.
+// when level 0 is queried in chunks, its per-region state.  `order` (one
+// block only): regions whose probe stays bounded from slot 0 up (count[0]),
+// the others from slot total - 1 down (back[0]); else in grid order.
 __global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, DevCounters *ctr,
-                            uint32_t n, uint32_t s0, uint32_t axis0, uint32_t row0, uint32_t rows)
+                            uint32_t n, uint32_t s0, uint32_t axis0, uint32_t row0, uint32_t rows,
+                            PixelMap pm, uint32_t order)
 {
+    __shared__ uint32_t s_front, s_back;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t total = axis0 * rows;
@@ -94,12 +119,31 @@ __global__ void init_kernel(uint2 *__restrict__ olt0, uint4 *__restrict__ rst0, 
     }
     if (olt0 == nullptr)
         return;
+    if (order) {
+        if (threadIdx.x == 0) {
+            s_front = 0;
+            s_back = 0;
+        }
+        __syncthreads();  // also orders the counter words above before the totals below
+    }
     for (uint32_t k = tid; k < total; k += stride) {
         const uint32_t gx = k % axis0, gy = row0 + k / axis0;
         const uint32_t x0 = gx * s0, y0 = gy * s0;
-        olt0[k] = pack_region(x0, y0, min(s0, n - x0), min(s0, n - y0));
+        const uint2 rec = pack_region(x0, y0, min(s0, n - x0), min(s0, n - y0));
+        uint32_t slot = k;
+        if (order)
+            slot = region_probe(pm, unpack_region(rec)) ? atomicAdd(&s_front, 1u)
+                                                        : total - 1u - atomicAdd(&s_back, 1u);
+        olt0[slot] = rec;
         if (rst0 != nullptr)
-            rst0[k] = make_uint4(kNone, 0u, 0u, 0u);
+            rst0[slot] = make_uint4(kNone, 0u, 0u, 0u);
+    }
+    if (order) {
+        __syncthreads();
+        if (threadIdx.x == 0 && ctr != nullptr) {
+            ctr->count[0] = s_front;
+            ctr->back[0] = s_back;
+        }
     }
 }
 
@@ -115,28 +159,11 @@ struct WarpBatch {
     uint32_t sc, r;  // child side and split factor of its frame
 };
 
-// Order hint for the leaf list: does the orbit of the leaf's centre pixel
-// stay bounded for kLeafProbe updates?  Such leaves hold most of the long
-// orbits (at n = 16384, dwell 2048: 16% of the leaves, 86% of the leaf
-// kernel's updates), so the leaf kernel takes them first and ends on leaves
-// whose orbits are short, and its warps run out of work together.  Only the
-// order of the leaves depends on it, never a dwell.  Unchecked updates: an
-// escaped orbit runs to inf or NaN and fails the test; where escape is not
-// absorbing the leaf counts as light.
+// Pixel map of a region record's frame.
 template <bool BATCH>
-__device__ __forceinline__ bool leaf_probe(const LevelArgs &a, const typename Rec<BATCH>::T &e)
+__device__ __forceinline__ PixelMap record_pm(const LevelArgs &a, const typename Rec<BATCH>::T &e)
 {
-    using R = Rec<BATCH>;
-    const Region g = R::region(e);
-    const PixelMap pm = BATCH ? a.frames[R::frame(e)].pm : a.pm;
-    const float2 c = pixel_c(pm, g.x0 + g.w / 2u, g.y0 + g.h / 2u);
-    if (!escape_absorbing(c.x, c.y))
-        return false;
-    float x = 0.0f, y = 0.0f;
-#pragma unroll 8
-    for (int k = 0; k < kLeafProbe; ++k)
-        z_update(x, y, c.x, c.y);
-    return z_bounded(x, y);
+    return BATCH ? a.frames[Rec<BATCH>::frame(e)].pm : a.pm;
 }
 
 template <bool BATCH>
@@ -154,7 +181,7 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH>
     const unsigned leaf_mask = __ballot_sync(kFull, b.kind == KIND_LEAF);
     if (leaf_mask) {
         const bool is_leaf = b.kind == KIND_LEAF;
-        const bool heavy = is_leaf && leaf_probe<BATCH>(a, b.rec);
+        const bool heavy = is_leaf && region_probe(record_pm<BATCH>(a, b.rec), R::region(b.rec));
         const unsigned hm = __ballot_sync(kFull, heavy), lm = leaf_mask & ~hm;
         uint32_t hb = 0, lb = 0;
         if (lane == 0) {
@@ -201,32 +228,55 @@ __device__ __forceinline__ void flush_batch(const LevelArgs &a, WarpBatch<BATCH>
                 atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
         }
     }
-    // children: warp inclusive scan of child counts, one atomicAdd
-    uint32_t incl = b.nchild;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (uint32_t)o)
-            incl += v;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total) {
-        uint32_t base = 0;
-        if (lane == 0)
-            base = atomicAdd(&ctr->count[a.level + 1], total);
-        base = __shfl_sync(kFull, base, 0);
-        if (b.nchild) {
-            const Region g = R::region(b.rec);
-            const uint32_t first = base + incl - b.nchild;
-            for (uint32_t j = 0; j < b.nchild; ++j) {
-                const uint32_t slot = first + j;
-                if (slot < a.olt_cap) {
-                    olt_out[slot] = R::child(b.rec, child_region(g, b.sc, b.r, j));
-                    if (a.next_chunks > 1u)
-                        a.rst_out[slot] = make_uint4(kNone, 0u, 0u, 0u);
-                } else {
-                    atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
+    // children: each lane probes its region's children (at most 64; a region
+    // with more sends them all to the front); warp inclusive scans of the
+    // counts going to the front and to the back of the next level's table,
+    // one atomicAdd for each
+    const unsigned split_any = __ballot_sync(kFull, b.nchild != 0u);
+    if (split_any) {
+        const Region g = R::region(b.rec);
+        unsigned long long heavy = ~0ull;  // bit j: child j goes to the front
+        uint32_t nh = b.nchild;
+        if (b.nchild != 0u && b.nchild <= 64u) {
+            const PixelMap pm = record_pm<BATCH>(a, b.rec);
+            heavy = 0ull;
+            nh = 0;
+            for (uint32_t j = 0; j < b.nchild; ++j)
+                if (region_probe(pm, unpack_region(child_region(g, b.sc, b.r, j)))) {
+                    heavy |= 1ull << j;
+                    ++nh;
                 }
+        }
+        const uint32_t nl = b.nchild - nh;
+        uint32_t ih = nh, il = nl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t vh = __shfl_up_sync(kFull, ih, o), vl = __shfl_up_sync(kFull, il, o);
+            if (lane >= (uint32_t)o) {
+                ih += vh;
+                il += vl;
+            }
+        }
+        const uint32_t th = __shfl_sync(kFull, ih, 31), tl = __shfl_sync(kFull, il, 31);
+        uint32_t hb = 0, lb = 0;
+        if (lane == 0) {
+            if (th)
+                hb = atomicAdd(&ctr->count[a.level + 1], th);
+            if (tl)
+                lb = atomicAdd(&ctr->back[a.level + 1], tl);
+        }
+        hb = __shfl_sync(kFull, hb, 0) + ih - nh;  // this lane's first front index
+        lb = __shfl_sync(kFull, lb, 0) + il - nl;  // and first back index
+        for (uint32_t j = 0; j < b.nchild; ++j) {
+            const bool front = (heavy >> (j & 63u)) & 1ull;
+            const uint32_t k = front ? hb++ : lb++;
+            if (k < a.out_cap) {
+                const uint32_t slot = front ? k : a.out_cap - 1u - k;
+                olt_out[slot] = R::child(b.rec, child_region(g, b.sc, b.r, j));
+                if (a.next_chunks > 1u)
+                    a.rst_out[slot] = make_uint4(kNone, 0u, 0u, 0u);
+            } else {
+                atomicOr(&ctr->error, ERR_OLT_OVERFLOW);
             }
         }
     }
@@ -280,7 +330,12 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t *stage = smem + (threadIdx.x >> 5) * kWarpStage;
     const T *olt_in = static_cast<const T *>(a.olt_in);
-    const uint32_t count = min(a.ctr->count[a.level], a.olt_cap);
+    // regions from the front of the table first, then those from the back
+    const uint32_t front = min(a.ctr->count[a.level], a.in_cap);
+    const uint32_t count = front + min(a.ctr->back[a.level], a.in_cap - front);
+    if (blockIdx.x == 0 && threadIdx.x == 0 &&
+        (unsigned long long)a.ctr->count[a.level] + a.ctr->back[a.level] > a.in_cap)
+        atomicOr(&a.ctr->error, ERR_OLT_OVERFLOW);
     const uint32_t chunks = a.chunks;
     const uint32_t items = count * chunks;  // the host keeps this below 2^32
 
@@ -302,7 +357,8 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
         t = __shfl_sync(kFull, t, 0);
         if (t >= items)
             break;
-        const uint32_t region = (chunks == 1u) ? t : t / chunks;
+        const uint32_t li = (chunks == 1u) ? t : t / chunks;  // in the order taken
+        const uint32_t region = table_slot(li, front, a.in_cap);  // its slot
         const T e = olt_in[region];
         const Region g = R::region(e);
         const FView f = BATCH ? view_frame(a.frames, R::frame(e), a.level) : view_single(a);
@@ -349,7 +405,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
                 }
             }
         } else {
-            const uint32_t c = t - region * chunks;
+            const uint32_t c = t - li * chunks;
             uint4 *st = a.rst_in + region;
             // one frame: chunks cover the level's largest perimeter; a batch
             // caps the chunk count, so a large region takes longer chunks
@@ -480,7 +536,7 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
     for (unsigned long long item = blockIdx.x; item < total; item += gridDim.x) {
         const uint32_t leaf = (uint32_t)(item / tiles_per_leaf);
         const uint32_t t = (uint32_t)(item - (unsigned long long)leaf * tiles_per_leaf);
-        const Region g = unpack_region(static_cast<const uint2 *>(a.leaves)[leaf_slot(leaf, front, leaf_cap)]);
+        const Region g = unpack_region(static_cast<const uint2 *>(a.leaves)[table_slot(leaf, front, leaf_cap)]);
         const uint32_t ty = t / tiles_x, tx = t - ty * tiles_x;
         const uint32_t px = g.x0 + tx * blockDim.x + threadIdx.x;
         const uint32_t py = g.y0 + ty * blockDim.y + threadIdx.y;
@@ -678,15 +734,20 @@ cudaError_t launch_exhaustive(uint32_t *map, uint32_t n, PixelMap pm, uint32_t m
 }
 
 cudaError_t launch_init(uint2 *olt0, uint4 *rst0, DevCounters *ctr, uint32_t n, uint32_t s0,
-                        uint32_t axis0, uint32_t row0, uint32_t rows, cudaStream_t s)
+                        uint32_t axis0, uint32_t row0, uint32_t rows, cudaStream_t s,
+                        const PixelMap *order)
 {
     const uint32_t total = axis0 * rows;
+    if (order != nullptr && olt0 != nullptr && total <= kInitOrderMax) {
+        init_kernel<<<1, 1024, 0, s>>>(olt0, rst0, ctr, n, s0, axis0, row0, rows, *order, 1u);
+        return cudaGetLastError();
+    }
     uint32_t blocks = (total + 255u) / 256u;
     if (blocks < 1)
         blocks = 1;
     if (blocks > 4096)
         blocks = 4096;
-    init_kernel<<<blocks, 256, 0, s>>>(olt0, rst0, ctr, n, s0, axis0, row0, rows);
+    init_kernel<<<blocks, 256, 0, s>>>(olt0, rst0, ctr, n, s0, axis0, row0, rows, PixelMap{}, 0u);
     return cudaGetLastError();
 }
 

@@ -217,6 +217,8 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
         a.olt_in = sc->olt[i & 1];
         a.olt_out = sc->olt[(i + 1) & 1];
         a.olt_cap = kNoAllocRegions;
+        a.in_cap = kNoAllocRegions;  // the tables fill from both ends of the whole array
+        a.out_cap = kNoAllocRegions;
         // one warp per region and fills in place: no per-region query state
         // or fill list, so the fixed scratch stays at three tables
         a.chunks = 1u;

@@ -349,12 +349,12 @@ __device__ __forceinline__ void cursor_at(LeafCursor &lc, const Region &g, uint3
     lc.inv_cw = 1.0f / (float)lc.cw;
 }
 
-// A leaf list is filled from both ends: leaf_count entries from the front
-// (the leaves likely to hold long orbits, or every leaf where the producer
-// does not order them) and leaf_light from the back.  Leaf t of the order in
-// which they are taken (the front first, then the back in append order) sits
-// at this slot.
-__device__ __forceinline__ uint32_t leaf_slot(uint32_t t, uint32_t front, uint32_t cap)
+// Region tables and leaf lists are filled from both ends: `front` entries
+// from slot 0 up (the regions or leaves likely to hold long orbits, or every
+// entry where the producer does not order them) and the rest from slot
+// cap - 1 down.  Entry t of the order in which they are taken (the front
+// first, then the back in append order) sits at this slot.
+__device__ __forceinline__ uint32_t table_slot(uint32_t t, uint32_t front, uint32_t cap)
 {
     return t < front ? t : cap - 1u - (t - front);
 }
@@ -387,7 +387,7 @@ struct LeafList {
         li = __shfl_sync(kFull, li, 0);
         if (li >= total)
             return SRC_DONE;
-        const typename R::T e = leaves[leaf_slot(li, front, cap)];
+        const typename R::T e = leaves[table_slot(li, front, cap)];
         cursor_at(lc, R::region(e), R::frame(e), a.skip_perimeter != 0u);
         return SRC_MORE;
     }
