@@ -109,7 +109,8 @@ static uint32_t ceil_div(uint32_t a, uint32_t b) { return a / b + (a % b != 0u);
 // its copy, and small bands leave the level kernels too few regions.
 constexpr uint64_t kBandBytes = 128ull << 20;
 
-bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px)
+bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px,
+               uint64_t few_items)
 {
     if (n == 0 || g == 0 || r < 2 || B == 0 || !plan)
         return false;
@@ -135,7 +136,11 @@ bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, 
         if (plan->max_regions[i] >= 0xffffffffull)
             return false;
         const uint64_t per = (s <= 2u) ? (uint64_t)s * s : 4ull * s - 4ull;
-        plan->chunks[i] = (uint32_t)((per + chunk_px - 1) / chunk_px);
+        uint32_t cp = chunk_px;
+        if (few_items && cp >= 64u && plan->max_regions[i] * ((per + cp - 1) / cp) < few_items)
+            cp /= 2u;
+        plan->chunk_px[i] = cp;
+        plan->chunks[i] = (uint32_t)((per + cp - 1) / cp);
         if (plan->max_regions[i] * plan->chunks[i] >= 0xffffffffull)
             return false;
         const uint32_t sc = ceil_div(s, r);
@@ -630,6 +635,7 @@ ask_status render_impl(ask_ctx *ctx, ask_method method, const ask_window *window
         a.in_cap = level_cap(i);
         a.out_cap = (i + 1 < L) ? level_cap(i + 1) : 0u;
         a.chunks = plan.chunks[i];
+        a.chunk_px = plan.chunk_px[i];
         a.next_chunks = (i + 1 < L) ? plan.chunks[i + 1] : 1u;
         a.rst_in = ctx->rst[i & 1];
         a.rst_out = ctx->rst[(i + 1) & 1];
@@ -774,7 +780,7 @@ ask_status plan_batch(ask_ctx *ctx, const ask_frame *frames, uint32_t nframes, u
         if (!fr.d_dwell || ((uintptr_t)fr.d_dwell & 15u))
             return set_err(ctx, ASK_EINVAL, "frame %u: d_dwell must be 16-byte aligned", f);
         LevelPlan plan;
-        if (!make_plan(fr.n, fr.g, fr.r, fr.B, &plan, kChunkPxBatch))
+        if (!make_plan(fr.n, fr.g, fr.r, fr.B, &plan, kChunkPxBatch, 0))
             return set_err(ctx, ASK_EINVAL, "frame %u: no valid subdivision plan", f);
         FrameDesc &d = bp.desc[f];
         std::memset(&d, 0, sizeof(d));

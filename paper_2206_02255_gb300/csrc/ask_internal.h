@@ -55,13 +55,23 @@ struct LevelPlan {
     uint32_t split[ASK_MAX_LEVELS];         // 1 if non-uniform regions of level i split
     uint64_t max_regions[ASK_MAX_LEVELS];   // upper bound on regions at level i
     uint32_t chunks[ASK_MAX_LEVELS];        // perimeter chunks per region (work items)
+    uint32_t chunk_px[ASK_MAX_LEVELS];      // perimeter pixels per chunk
     uint32_t axis0;                         // non-empty initial regions per axis
 };
 
+// A level with fewer work items than this at chunk_px pixels a chunk takes
+// chunks of half that size: its items are too few to keep every warp busy,
+// and the kernel's time is set by its longest items (chunks of a region
+// inside the set run max_dwell updates per pixel, one pixel per lane after
+// another).
+constexpr uint64_t kFewLevelItems = 32768;
+
 // Fills `plan`; returns false if the parameters are invalid or a level could
 // hold 2^32 regions or more.
-// chunk_px: perimeter pixels per work item of the level kernels (chunks[i]).
-bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px = 64);
+// chunk_px: perimeter pixels per work item of the level kernels (chunks[i]);
+// few_items: levels with fewer items take chunks of chunk_px / 2 (0: never).
+bool make_plan(uint32_t n, uint32_t g, uint32_t r, uint32_t B, LevelPlan *plan, uint32_t chunk_px = 64,
+               uint64_t few_items = kFewLevelItems);
 
 // Launch configuration chosen per device at context creation.
 struct DeviceInfo {
@@ -122,6 +132,7 @@ struct LevelArgs {
                           //   slot in_cap - 1 down
     uint32_t out_cap;     // the same bound for the next level's table (olt_out, rst_out)
     uint32_t chunks;      // perimeter chunks per region at this level (1 = one warp per region)
+    uint32_t chunk_px;    // perimeter pixels per chunk (one frame; a batch derives its own)
     uint32_t next_chunks; // chunks per region at the next level
     uint4 *rst_in;        // per-region query state of this level (chunks > 1)
     uint4 *rst_out;       // state of the next level's regions, set when they are appended

@@ -18,9 +18,12 @@
 //    region count from device memory and hand out work with an atomic
 //    counter, so no depth needs a host round trip;
 //  * a work item is one region's perimeter, or one chunk of kChunkPx
-//    (kChunkPxBatch in a batch) perimeter pixels of a large region (several
-//    warps per region: the MBR mapping of Sec. 4.3.2 applied to the query),
-//    one warp per item;
+//    (kChunkPxBatch in a batch; half of kChunkPx at a level with few items)
+//    perimeter pixels of a large region (several warps per region: the MBR
+//    mapping of Sec. 4.3.2 applied to the query), one warp per item;
+//  * each region table is filled from both ends (regions whose centre orbit
+//    stays bounded for a short probe from the front), so a level kernel
+//    takes its longest regions first; the leaf list likewise;
 //  * a query stops at the first two perimeter dwells known to differ; warps
 //    of one region share that verdict through a per-region state word, and
 //    the warp that finishes the region's last chunk takes the decision;
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
             uint4 *st = a.rst_in + region;
             // one frame: chunks cover the level's largest perimeter; a batch
             // caps the chunk count, so a large region takes longer chunks
-            const uint32_t CP = BATCH ? max(kChunkPxBatch, ceil_div_u32(P, chunks)) : kChunkPx;
+            const uint32_t CP = BATCH ? max(kChunkPxBatch, ceil_div_u32(P, chunks)) : a.chunk_px;
             const uint32_t k0 = min(P, c * CP), k1 = min(P, k0 + CP);
             if (COUNT && lane == 0)
                 bpx += k1 - k0;

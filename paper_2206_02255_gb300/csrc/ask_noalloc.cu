@@ -222,6 +222,7 @@ extern "C" ask_status ask_render_noalloc(const ask_window *window, uint32_t n, u
         // one warp per region and fills in place: no per-region query state
         // or fill list, so the fixed scratch stays at three tables
         a.chunks = 1u;
+        a.chunk_px = kChunkPx;
         a.next_chunks = 1u;
         a.rst_in = nullptr;
         a.rst_out = nullptr;
