@@ -175,6 +175,38 @@ __device__ __forceinline__ void orbit_resolve(Orbit &o)
     o.d = d + 1u;
 }
 
+// Rounds of a perimeter query: unchecked blocks of 8, 8 and 16 updates, then
+// K.  Most perimeter orbits outside the set escape within a few updates; a
+// short first block and the short binary search after it cost them about 15
+// updates where a K-update block and its search cost 2K - 1, while an orbit
+// that runs long pays three short rounds.  Every lane of a group runs the
+// same block in a round, so a running orbit still outlives every orbit that
+// finished in that round.
+template <uint32_t K>
+__device__ __forceinline__ void query_step(Orbit &o, uint32_t &stt, uint32_t limit, uint32_t rnd)
+{
+    if (stt != ORBIT_RUN)
+        return;
+    if (rnd < 2u)
+        stt = orbit_step<8>(o, limit);
+    else if (rnd == 2u)
+        stt = orbit_step<16>(o, limit);
+    else
+        stt = orbit_step<K>(o, limit);
+}
+
+// Exact dwell of an orbit left pending by query_step<K> in round `rnd`.
+template <uint32_t K>
+__device__ __forceinline__ void query_resolve(Orbit &o, uint32_t rnd)
+{
+    if (rnd < 2u)
+        orbit_resolve<8>(o);
+    else if (rnd == 2u)
+        orbit_resolve<16>(o);
+    else
+        orbit_resolve<K>(o);
+}
+
 // Region record of the offset lookup tables (Sec. 5.2): origin and clipped
 // extent, 16 bits each (n <= 65536 so x0, y0, w-1, h-1 < 65536).
 struct Region {
@@ -322,9 +354,9 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
         uint32_t stt = active ? ORBIT_RUN : ORBIT_DONE;
         const uint32_t limit = have ? min(max_dwell, w + 1u) : max_dwell;
         bool differ = false;
-        for (;;) {
-            if (stt == ORBIT_RUN)
-                stt = orbit_step<kQueryRound>(o, limit);
+        uint32_t rnd = 0;
+        for (;; ++rnd) {
+            query_step<kQueryRound>(o, stt, limit, rnd);
             const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -333,8 +365,9 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
                 break;
             }
         }
+        // every orbit finished in round rnd (else they would differ)
         if (!differ && stt == ORBIT_PEND)
-            orbit_resolve<kQueryRound>(o);
+            query_resolve<kQueryRound>(o, rnd);
         if (active)
             it += o.d;
         if (differ)

@@ -87,6 +87,11 @@ __device__ __forceinline__ FView view_frame(const FrameDesc *frames, uint32_t f,
 // batch keeps enough warps resident to hide the load, and there a late
 // stop costs more than the wait, so it uses the value one round later.
 constexpr uint32_t kPollLag = 8;
+// Chunked queries of regions with longer perimeters skip the short first
+// rounds of query_step (at n = 16384 they slowed levels 0 and 1, whose
+// regions of side 1024 and 256 are seldom uniform outside the set, and sped
+// up level 2, side 64).
+constexpr uint32_t kShortRoundsMaxPerimeter = 512;
 
 // One chunk [k0, k1) of a large region's perimeter, queried by one warp.  The
 // region's state st: x = common dwell found so far (kNone: none yet),
@@ -122,15 +127,17 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
         // batch) and consumed that many rounds later, so its L2 latency
         // hides behind the updates of those rounds; a stale value is
         // harmless (the common dwell is set once, the flag only rises).
+        // short first rounds for small regions only: large ones are mostly
+        // inside the set or on its boundary, rarely uniform outside it
         uint32_t nx = v.x, ny = v.y, lag = 0;
-        for (;;) {
+        uint32_t rnd = perimeter_size(g.w, g.h) > kShortRoundsMaxPerimeter ? 3u : 0u;
+        for (;; ++rnd) {
             if (lag == 0 && lane == 0) {
                 nx = ps[0];
                 ny = ps[1];
             }
             const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
-            if (stt == ORBIT_RUN)
-                stt = orbit_step<kQueryRoundLarge>(o, limit);
+            query_step<kQueryRoundLarge>(o, stt, limit, rnd);
             const unsigned dm = __ballot_sync(kFull, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -148,8 +155,9 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
                 }
             }
         }
+        // every orbit finished in round rnd (else they would differ)
         if (!stop && !differ && stt == ORBIT_PEND)
-            orbit_resolve<kQueryRoundLarge>(o);
+            query_resolve<kQueryRoundLarge>(o, rnd);
         if (active)
             it += o.d;
         if (stop)
