@@ -112,11 +112,17 @@ enum : uint32_t {
                      // (o.d, o.d + K], o keeps the block's starting state
 };
 
-// Updates per unchecked block of a perimeter-query round: a large region's
-// chunks (many rounds, few warps) take long rounds; a small region's whole
-// perimeter takes shorter ones, since its group ends after few rounds.
+// Updates per unchecked block of a perimeter-query round after the short
+// first rounds of query_step, for a large region's chunks and for a small
+// region's whole perimeter.  The short rounds take the orbits that escape
+// early, so the long ones serve orbits that run long (at n = 16384 whole
+// perimeters of 16 x 16 regions ran faster with 64 than with 32; chunks ran
+// slower with 128).
 constexpr uint32_t kQueryRoundLarge = 64;
-constexpr uint32_t kQueryRound = 32;
+constexpr uint32_t kQueryRound = 64;
+// The CTA-wide query of the paper's SBR / MBR mappings: blocks of 32 from
+// the first round.
+constexpr uint32_t kQueryRoundCta = 32;
 
 // Advance an orbit by up to K updates (a power of two) without passing
 // `limit`.  An orbit still running after a round has made more updates than
@@ -413,7 +419,7 @@ __device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32
             const uint32_t wv = __shfl_sync(kLaneMask, *vw, 0);
             const uint32_t limit = (wv != 0xffffffffu) ? min(max_dwell, wv + 1u) : max_dwell;
             if (stt == ORBIT_RUN)
-                stt = orbit_step<kQueryRound>(o, limit);
+                stt = orbit_step<kQueryRoundCta>(o, limit);
             const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -427,7 +433,7 @@ __device__ __forceinline__ bool cta_perimeter_uniform(const PixelMap &pm, uint32
             }
         }
         if (!stop && !differ && stt == ORBIT_PEND)
-            orbit_resolve<kQueryRound>(o);
+            orbit_resolve<kQueryRoundCta>(o);
         if (active)
             it += o.d;
         if (stop)
