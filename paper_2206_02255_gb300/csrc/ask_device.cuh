@@ -123,6 +123,13 @@ constexpr uint32_t kQueryRound = 64;
 // The CTA-wide query of the paper's SBR / MBR mappings: blocks of 32 from
 // the first round.
 constexpr uint32_t kQueryRoundCta = 32;
+// Batches (zoomed frames, higher dwell caps, regions of many sizes): whole
+// perimeters in blocks of kQueryRoundBatch, short first rounds where the
+// flags say (a batch's chunk queries read their region's state every round,
+// and a short round cannot hide that load).
+constexpr uint32_t kQueryRoundBatch = 32;
+constexpr bool kBatchShortWhole = false;
+constexpr bool kBatchShortChunks = false;
 
 // Advance an orbit by up to K updates (a power of two) without passing
 // `limit`.  An orbit still running after a round has made more updates than
@@ -342,6 +349,7 @@ constexpr unsigned kLaneMask = 0xffffffffu;
 
 // One warp queries the whole perimeter of g.  Returns true and the common
 // dwell in *w_out if the perimeter is uniform; `it` gains the updates made.
+template <uint32_t K, bool SHORT>
 __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint32_t max_dwell,
                                                        const Region &g, uint32_t lane,
                                                        uint32_t *w_out, unsigned long long &it)
@@ -362,7 +370,10 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
         bool differ = false;
         uint32_t rnd = 0;
         for (;; ++rnd) {
-            query_step<kQueryRound>(o, stt, limit, rnd);
+            if (SHORT)
+                query_step<K>(o, stt, limit, rnd);
+            else if (stt == ORBIT_RUN)
+                stt = orbit_step<K>(o, limit);
             const unsigned dm = __ballot_sync(kLaneMask, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -372,8 +383,12 @@ __device__ __forceinline__ bool warp_perimeter_uniform(const PixelMap &pm, uint3
             }
         }
         // every orbit finished in round rnd (else they would differ)
-        if (!differ && stt == ORBIT_PEND)
-            query_resolve<kQueryRound>(o, rnd);
+        if (!differ && stt == ORBIT_PEND) {
+            if (SHORT)
+                query_resolve<K>(o, rnd);
+            else
+                orbit_resolve<K>(o);
+        }
         if (active)
             it += o.d;
         if (differ)

@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(256) level_kernel(LevelArgs a)
             if (COUNT && lane == 0)
                 bpx += P;
             if (query) {
-                uniform = warp_perimeter_uniform(f.pm, f.max_dwell, g, lane, &wv, it);
+                uniform = warp_perimeter_uniform<BATCH ? kQueryRoundBatch : kQueryRound, !BATCH || kBatchShortWhole>(
+                    f.pm, f.max_dwell, g, lane, &wv, it);
             } else {
                 // last level, exact perimeters staged in shared memory: a leaf
                 // keeps them and the leaf kernel skips them

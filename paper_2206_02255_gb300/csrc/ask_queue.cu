@@ -233,7 +233,7 @@ __device__ __forceinline__ void process_item(const QueueArgs &q, uint32_t t, uin
     uint32_t wv = 0;
     if (C <= 1u) {
         decided = true;
-        uniform = warp_perimeter_uniform(f.pm, f.max_dwell, g, lane, &wv, it);
+        uniform = warp_perimeter_uniform<kQueryRoundBatch, kBatchShortWhole>(f.pm, f.max_dwell, g, lane, &wv, it);
     } else {
         uint4 *st = q.rst + aux;
         const uint32_t CP = max(q.chunk_px, ceil_div_u32(P, C));

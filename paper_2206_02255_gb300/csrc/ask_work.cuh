@@ -130,14 +130,18 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
         // short first rounds for small regions only: large ones are mostly
         // inside the set or on its boundary, rarely uniform outside it
         uint32_t nx = v.x, ny = v.y, lag = 0;
-        uint32_t rnd = perimeter_size(g.w, g.h) > kShortRoundsMaxPerimeter ? 3u : 0u;
+        constexpr bool kShort = !BATCH || kBatchShortChunks;
+        uint32_t rnd = (kShort && perimeter_size(g.w, g.h) <= kShortRoundsMaxPerimeter) ? 0u : 3u;
         for (;; ++rnd) {
             if (lag == 0 && lane == 0) {
                 nx = ps[0];
                 ny = ps[1];
             }
             const uint32_t limit = (v.x != kNone) ? min(a.max_dwell, v.x + 1u) : a.max_dwell;
-            query_step<kQueryRoundLarge>(o, stt, limit, rnd);
+            if (kShort)
+                query_step<kQueryRoundLarge>(o, stt, limit, rnd);
+            else if (stt == ORBIT_RUN)
+                stt = orbit_step<kQueryRoundLarge>(o, limit);
             const unsigned dm = __ballot_sync(kFull, stt != ORBIT_RUN) & amask;
             if (dm == amask)
                 break;
@@ -156,8 +160,12 @@ __device__ __forceinline__ void chunk_query(const FView &a, const Region &g, uin
             }
         }
         // every orbit finished in round rnd (else they would differ)
-        if (!stop && !differ && stt == ORBIT_PEND)
-            query_resolve<kQueryRoundLarge>(o, rnd);
+        if (!stop && !differ && stt == ORBIT_PEND) {
+            if (kShort)
+                query_resolve<kQueryRoundLarge>(o, rnd);
+            else
+                orbit_resolve<kQueryRoundLarge>(o);
+        }
         if (active)
             it += o.d;
         if (stop)
