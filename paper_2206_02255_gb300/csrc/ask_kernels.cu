@@ -48,7 +48,7 @@ namespace ask {
 namespace {
 
 constexpr uint32_t kWarpStage = 512;  // staged perimeter pixels per warp (exact last level)
-constexpr int kLeafProbe = 64;        // updates of a leaf's order probe
+constexpr int kOrderProbe = 64;       // updates of the order probe (region_probe)
 
 enum : uint32_t { KIND_NONE = 0, KIND_FILL = 1, KIND_SPLIT = 2, KIND_LEAF = 3, KIND_FILL_LATER = 4 };
 
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(1024) exhaustive_kernel(uint32_t *__restrict__
 
 // Order probe of a region (the order in which the region tables and the
 // leaf list are taken): does the orbit of the region's centre pixel stay
-// bounded for kLeafProbe updates?  Regions inside the set, whose perimeter
+// bounded for kOrderProbe updates?  Regions inside the set, whose perimeter
 // orbits all run to max_dwell, and leaves holding such orbits answer yes;
 // taking them first lets a kernel's warps run out of work together instead
 // of ending on a wave of its longest items.  Only the order of the work
@@ -94,7 +94,7 @@ __device__ __forceinline__ bool region_probe(const PixelMap &pm, const Region &g
         return false;
     float x = 0.0f, y = 0.0f;
 #pragma unroll 8
-    for (int k = 0; k < kLeafProbe; ++k)
+    for (int k = 0; k < kOrderProbe; ++k)
         z_update(x, y, c.x, c.y);
     return z_bounded(x, y);
 }
