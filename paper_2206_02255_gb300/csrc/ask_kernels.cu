@@ -595,7 +595,12 @@ __global__ void __launch_bounds__(1024) leaf_kernel(LeafArgs a, uint32_t leaf_ca
 //    lane: a binary search over the parked block finds the exact escape (the
 //    block's midpoint state is parked too, so the first halving costs one
 //    test; then unchecked quarter, eighth, ... blocks and one test each, the
-//    same number of steps on every lane), and the dwells are written.
+//    same number of steps on every lane), and the dwells are written;
+//  * the leaves are taken in the order of the list, whose front holds the
+//    leaves whose centre orbit the level kernel's probe found bounded (most
+//    long orbits), so the warps end on short orbits; once the list has run
+//    out and a warp's orbits fit in one slot per lane, slot 1 folds into
+//    slot 0 and the last rounds update one orbit per lane.
 // ---------------------------------------------------------------------------
 // The leaf kernel over the leaf list of a launch chain.  Each lane of the
 // refill loop carries two independent orbits, so one round's bookkeeping
